@@ -1,0 +1,214 @@
+"""One-level ORAS preconditioner and flexible GMRES (Section 3), plain CPU form.
+
+Decomposition (Section 3):
+* non-overlapping partition T_i of the tets by recursive coordinate bisection
+  of tet centroids (the paper uses a graph partitioner; any partition is
+  admissible).  At each step the tets are sorted by (centroid[axis], tet id)
+  along the axis of largest centroid extent (lowest axis on ties) and split
+  at floor(|T| p_left / p) with p_left = p // 2;
+* overlap: T_i^d = T_i^{d-1} plus every tet adjacent to it, where adjacent
+  means sharing a vertex;
+* P1 partition of unity (Eq. chi): chi~_i = 1 at the nodes of T_i^0 and 0 at
+  the other nodes of T_i^delta; chi_i = chi~_i / sum_j chi~_j;
+* edge partition of unity: D_i[e] = chi_i at the midpoint of edge e (face
+  DOFs of order 2: at the face centroid), so sum_i R_i^T D_i R_i = I
+  (Eq. algebPartUnity);
+* local operator B_i: the form of Eq. pbdirectvarf restricted to T_i^delta,
+  plus the impedance condition i k int (E x n).(v x n) on the faces of
+  T_i^delta interior to the domain, k = k0 sqrt(eps_t) of the tet of
+  T_i^delta owning the face.
+
+ORAS (Eq. ORAS):  M^{-1} r = sum_i R_i^T D_i B_i^{-1} R_i r, each B_i^{-1} by
+sparse LU.  FGMRES: right-preconditioned flexible GMRES (restarted, x0 = 0,
+modified Gram-Schmidt Arnoldi, Givens rotations), stopped on the
+unpreconditioned relative residual (Section 6).
+"""
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from .assemble import _scatter_symmetric
+from .constants import k0_of
+from .fem import element_matrices, face_matrix
+
+
+def rcb_partition(xyz, tet, nparts):
+    c = xyz[np.asarray(tet)].sum(axis=1) / 4.0
+    part = np.zeros(c.shape[0], dtype=np.int64)
+
+    def rec(ids, p, first):
+        if p == 1:
+            part[ids] = first
+            return
+        cc = c[ids]
+        ext = cc.max(axis=0) - cc.min(axis=0)
+        ax = int(np.argmax(ext))
+        order = np.lexsort((ids, cc[:, ax]))
+        ids = ids[order]
+        pl = p // 2
+        cut = (ids.size * pl) // p
+        rec(ids[:cut], pl, first)
+        rec(ids[cut:], p - pl, first + pl)
+
+    rec(np.arange(c.shape[0]), int(nparts), 0)
+    return part
+
+
+def grow_overlap(tet, in_sub, delta):
+    """T^d: add every tet sharing a vertex with T^{d-1}, delta times."""
+    tet = np.asarray(tet)
+    sub = in_sub.copy()
+    nv = int(tet.max()) + 1
+    for _ in range(delta):
+        vm = np.zeros(nv, dtype=bool)
+        vm[tet[sub].ravel()] = True
+        sub = vm[tet].any(axis=1)
+    return sub
+
+
+class Decomposition:
+    def __init__(self, xyz, tet, topo, part, delta=1):
+        self.nsub = int(part.max()) + 1
+        self.part = part
+        tet = np.asarray(tet)
+        nv = xyz.shape[0]
+        self.T0 = [part == i for i in range(self.nsub)]
+        self.Td = [grow_overlap(tet, m, delta) for m in self.T0]
+        chit = np.zeros((self.nsub, nv))
+        for i in range(self.nsub):
+            chit[i, np.unique(tet[self.T0[i]])] = 1.0
+        chi = chit / chit.sum(axis=0, keepdims=True)
+        self.chi = chi
+        self.R, self.D = [], []
+        for i in range(self.nsub):
+            d = topo.tet_dofs[self.Td[i]].ravel()
+            dofs = np.unique(d[d >= 0])
+            self.R.append(dofs)
+            vv = topo.dof_verts[dofs]
+            cnt = (vv >= 0).sum(axis=1)
+            vals = np.where(vv >= 0, chi[i][np.maximum(vv, 0)], 0.0).sum(axis=1) / cnt
+            self.D.append(vals)
+
+
+def local_matrices(xyz, topo, dec, eps, freq, K=None, M=None):
+    """B_i for every subdomain, in the local numbering given by dec.R[i]."""
+    eps = np.asarray(eps, dtype=np.complex128)
+    k0 = k0_of(freq)
+    if K is None or M is None:
+        K, M = element_matrices(xyz, topo)
+    vol = K.astype(np.complex128) - (k0 * k0) * eps[:, None, None] * M
+    out = []
+    for i in range(dec.nsub):
+        inside = dec.Td[i]
+        tets = np.nonzero(inside)[0]
+        # faces of T_i^delta on its boundary: one tet of the face inside, the other outside or absent
+        ft_all, fl_all, kind = [], [], []
+        for s in range(2):
+            t = topo.face_tets[:, s]
+            o = topo.face_tets[:, 1 - s]
+            ok = (t >= 0) & inside[np.maximum(t, 0)]
+            other_out = (o < 0) | ~inside[np.maximum(o, 0)]
+            sel = np.nonzero(ok & other_out)[0]
+            ft_all.append(t[sel])
+            fl_all.append(topo.face_local[sel, s])
+            kind.append(topo.face_tag[sel])
+        ft = np.concatenate(ft_all)
+        fl = np.concatenate(fl_all)
+        fk = np.concatenate(kind)
+        use = fk != 1  # PEC faces carry no term (their DOFs are removed)
+        ft, fl = ft[use], fl[use]
+        B = face_matrix(xyz, topo, ft, fl)
+        kb = k0 * np.sqrt(eps[ft])
+        g2l = -np.ones(topo.ndof + 1, dtype=np.int64)
+        g2l[dec.R[i]] = np.arange(dec.R[i].size)
+        dl_t = g2l[topo.tet_dofs[tets]]
+        dl_f = g2l[topo.tet_dofs[ft]]
+        dofs = np.concatenate([dl_t, dl_f], axis=0)
+        vals = np.concatenate([vol[tets], 1j * kb[:, None, None] * B], axis=0)
+        out.append(_scatter_symmetric(dofs, vals, dec.R[i].size))
+    return out
+
+
+class ORAS:
+    def __init__(self, dec, Bs):
+        self.dec = dec
+        self.lus = [spla.splu(B.tocsc(), permc_spec="MMD_AT_PLUS_A") for B in Bs]
+
+    def apply(self, r):
+        r = np.asarray(r, dtype=np.complex128)
+        z = np.zeros_like(r)
+        for i, lu in enumerate(self.lus):
+            Ri = self.dec.R[i]
+            yi = lu.solve(np.ascontiguousarray(r[Ri]))
+            Di = self.dec.D[i]
+            z[Ri] += Di.reshape((-1,) + (1,) * (r.ndim - 1)) * yi
+        return z
+
+
+def fgmres(A, b, precond, rtol=1e-8, restart=50, maxiter=1000):
+    """Right-preconditioned flexible GMRES for one column (Saad, Alg. 9.6)."""
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.size
+    x = np.zeros(n, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, [0.0]
+    hist = []
+    it = 0
+    r = b.copy()
+    beta = np.linalg.norm(r)
+    hist.append(beta / bnorm)
+    while it < maxiter and beta / bnorm > rtol:
+        V = np.zeros((restart + 1, n), dtype=np.complex128)
+        Z = np.zeros((restart, n), dtype=np.complex128)
+        H = np.zeros((restart + 1, restart), dtype=np.complex128)
+        cs = np.zeros(restart, dtype=np.complex128)
+        sn = np.zeros(restart, dtype=np.complex128)
+        g = np.zeros(restart + 1, dtype=np.complex128)
+        g[0] = beta
+        V[0] = r / beta
+        k_done = 0
+        for k in range(restart):
+            Z[k] = precond(V[k])
+            w = A @ Z[k]
+            for i in range(k + 1):
+                H[i, k] = np.vdot(V[i], w)
+                w = w - H[i, k] * V[i]
+            H[k + 1, k] = np.linalg.norm(w)
+            if H[k + 1, k] != 0.0:
+                V[k + 1] = w / H[k + 1, k]
+            for i in range(k):
+                t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+                H[i + 1, k] = -np.conj(sn[i]) * H[i, k] + np.conj(cs[i]) * H[i + 1, k]
+                H[i, k] = t
+            a, bb = H[k, k], H[k + 1, k]
+            den = np.sqrt(abs(a) ** 2 + abs(bb) ** 2)
+            # unitary rotation [c s; -conj(s) conj(c)] mapping [a; b] to [den; 0]
+            cs[k] = np.conj(a) / den if den != 0 else 1.0
+            sn[k] = np.conj(bb) / den if den != 0 else 0.0
+            H[k, k] = cs[k] * a + sn[k] * bb
+            H[k + 1, k] = 0.0
+            g[k + 1] = -np.conj(sn[k]) * g[k]
+            g[k] = cs[k] * g[k]
+            it += 1
+            k_done = k + 1
+            hist.append(abs(g[k + 1]) / bnorm)
+            if abs(g[k + 1]) / bnorm <= rtol or it >= maxiter:
+                break
+        y = np.linalg.solve(np.triu(H[:k_done, :k_done]), g[:k_done])
+        x = x + Z[:k_done].T @ y
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        hist[-1] = beta / bnorm
+    return x, it, hist
+
+
+def solve_oras(A, B, oras, rtol=1e-10, restart=50, maxiter=1000):
+    """FGMRES + ORAS for every column of B; returns U, iteration counts."""
+    B = np.asarray(B, dtype=np.complex128)
+    U = np.zeros_like(B)
+    its = []
+    for j in range(B.shape[1]):
+        U[:, j], it, _ = fgmres(A, B[:, j], oras.apply, rtol=rtol, restart=restart, maxiter=maxiter)
+        its.append(it)
+    return U, its
