@@ -1,0 +1,221 @@
+/*
+ * mwi.h -- C ABI of the GB300 microwave-imaging solver (libmwi.so).
+ *
+ * The library computes, on one GPU, the hot path of the paper's inversion
+ * (Tournier et al., "Microwave Tomographic Imaging of Cerebrovascular
+ * Accidents by Using High-Performance Computing"):
+ *
+ *   1. the time-harmonic curl-curl Maxwell problem (Section 2, Eq. pbdirect)
+ *      discretised by Nedelec edge elements of degree 1 or 2 (Section 2.1),
+ *      giving one linear system A u_j = b_j per transmitting antenna, all with
+ *      the same complex-symmetric A (Eq. linsys);
+ *   2. its solution by right-preconditioned flexible GMRES with the one-level
+ *      ORAS preconditioner M^-1 = sum_i R_i^T D_i B_i^-1 R_i (Section 3,
+ *      Eq. ORAS), all subdomains factorised and applied as one batch;
+ *   3. the S-parameters (Section 4, Eq. sij), the misfit J (Section 5,
+ *      Eq. defJ), the adjoint problem (Eq. pbadj) solved with the same
+ *      operator and factors, and the per-tetrahedron gradient dJ/d eps_r.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im) pairs of double.
+ * - Time factor exp(+i omega t): lossy media have Im(eps_r) < 0.  The
+ *   factorisation runs without pivoting and relies on Im(A) being positive
+ *   definite, which holds when every tet has Im(eps_r) < 0 (the LDL^T of a
+ *   complex-symmetric matrix with positive-definite imaginary part exists).
+ *   A pivot that still falls below a tiny threshold is perturbed and
+ *   reported through mwi_solve_info.n_perturbed; FGMRES absorbs it.
+ * - Ownership: every input array is caller-owned and copied (or read) during
+ *   the call; every output array is caller-allocated.  Handles own all of
+ *   their device memory.
+ * - Errors: no C++ exception or abort crosses this boundary.  Every entry
+ *   point returns an mwi_status; on a non-OK status mwi_last_error() returns
+ *   a thread-local, human-readable message.  MWI_ENOTCONV still fills the
+ *   outputs and the info struct.
+ * - Streams: a problem's device work is ordered on the CUDA stream given to
+ *   mwi_assemble (0 = the legacy default stream).  Calls return after that
+ *   work has completed.  One handle must be used by one host thread at a time.
+ * - Arrays marked "device" are device pointers on the current CUDA device;
+ *   all others are host pointers.
+ */
+#ifndef MWI_H
+#define MWI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MWI_OK = 0,
+    MWI_EINVAL = 1,     /* bad argument (size, pointer, value) */
+    MWI_ENOMEM = 2,     /* host or device allocation failed */
+    MWI_ENOTCONV = 3,   /* FGMRES hit max_iter before rtol on some column */
+    MWI_ECUDA = 4,      /* a CUDA runtime call failed */
+    MWI_ETIMEOUT = 5,   /* reserved: bounded wait expired */
+    MWI_ESTATE = 6,     /* call out of order (e.g. gradient before forward) */
+    MWI_ESINGULAR = 7   /* a zero pivot could not be perturbed */
+} mwi_status;
+
+typedef struct mwi_mesh* mwi_mesh_t;       /* opaque: topology, DOFs, element geometry */
+typedef struct mwi_problem* mwi_problem_t; /* opaque: A, ORAS factors, resident fields */
+
+/* Edge-current dipole antenna (the paper's waveguide ports are replaced by a
+ * current I on one mesh edge): the edge starts at the mesh vertex nearest to
+ * pos and is the edge at that vertex best aligned with dir (ties: lowest
+ * vertex id, then lowest edge id in (low, high) vertex-id order). */
+typedef struct {
+    double pos[3];
+    double dir[3];
+    double re_I, im_I;
+} mwi_antenna;
+
+/* Solver options.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+    double rtol;          /* outer FGMRES relative residual, true ||b - A u|| / ||b|| [1e-6] */
+    int32_t max_iter;     /* outer iterations per column, hard limit [500] */
+    int32_t restart;      /* outer FGMRES restart length [50] */
+    int32_t n_sub;        /* ORAS subdomains N_S [64] */
+    int32_t overlap;      /* overlap delta in vertex-adjacent tet layers [1]; < 0 means none */
+    int32_t precision;    /* 0 = complex FP64 everywhere; 1 = MIXED: complex FP32 subdomain
+                             factors and inner GMRES inside FP64 outer FGMRES [0] */
+    int32_t inner_iters;  /* MIXED: inner GMRES iterations per outer step [30] */
+    double inner_rtol;    /* MIXED: inner relative residual target [1e-4] */
+    int32_t nd_leaf;      /* nested-dissection leaf size of the subdomain ordering [64] */
+    int32_t verbose;      /* 0 silent, 1 phase timings on stderr [0] */
+    const int32_t* part;  /* optional [nt] host array: caller's tet -> subdomain map
+                             (values in [0, n_sub)); NULL = recursive coordinate bisection */
+} mwi_solver_opts;
+
+typedef struct {
+    int32_t iters_max;    /* largest outer iteration count over columns */
+    int32_t inner_total;  /* MIXED: inner iterations summed over outer steps */
+    int32_t n_converged;  /* columns whose true relative residual <= rtol */
+    int32_t n_perturbed;  /* pivots perturbed in the factorisation */
+    double resid_max;     /* largest true relative residual over columns */
+    double setup_ms;      /* assemble + factorise (mwi_assemble only) */
+    double solve_ms;      /* FGMRES wall time of this call */
+} mwi_solve_info;
+
+/* ---------------------------------------------------------------------- */
+/* Mesh: Section 2.1 (edge elements on a tetrahedral mesh).
+ * xyz [nv*3] vertex coordinates (m); tet [nt*4] vertex ids; bface_tag [nt*4]
+ * tag of the face opposite local vertex k: 0 interior, 1 perfectly conducting
+ * (Eq. eqmetal: its DOFs are removed), 2 impedance (Eq. eqwgi with
+ * beta = k0 sqrt(eps_r) of the owning tet).  order = 1 (Whitney, 6 DOFs/tet)
+ * or 2 (hierarchical first kind, 20 DOFs/tet).  Builds edges/faces, DOF
+ * numbering, and the element geometric integrals on the current device.
+ * Returns MWI_EINVAL for a degenerate tet or bad ids. */
+mwi_status mwi_mesh_create(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                           const int32_t* bface_tag, int32_t order, mwi_mesh_t* out);
+
+/* Number of DOFs after PEC removal. */
+mwi_status mwi_mesh_ndof(mwi_mesh_t mesh, int64_t* ndof);
+
+/* Identity of every DOF in the library's internal order: kind[ndof]
+ * (0 Whitney edge, 1 edge gradient, 2 face lambda_c N_ab, 3 face lambda_a N_bc)
+ * and verts[ndof*3] (global vertex ids in increasing order; third = -1 for
+ * edge DOFs).  Lets a caller map fields to its own numbering. */
+mwi_status mwi_mesh_dof_keys(mwi_mesh_t mesh, int32_t* kind, int64_t* verts);
+
+/* Destroys a mesh; MWI_ESTATE if a problem still references it. */
+mwi_status mwi_mesh_destroy(mwi_mesh_t mesh);
+
+/* ---------------------------------------------------------------------- */
+/* Assemble A = K - k0^2 sum_t eps_t M_t + i sum_f beta_f B_f (Eq. pbdirectvarf,
+ * Eq. linsys) for eps_r [nt] (interleaved complex, host) at freq_hz, build the
+ * ORAS decomposition of Section 3 (partition, delta-overlap, P1 partition of
+ * unity interpolated at edge midpoints, local operators B_i with impedance
+ * transmission conditions, k = k0 sqrt(eps_t) of the owning tet) and factorise
+ * every B_i as one batch (LDL^T, nested-dissection multifrontal, FP64 or
+ * FP32 per opts.precision).  cuda_stream: a cudaStream_t (0 = default). */
+mwi_status mwi_assemble(mwi_mesh_t mesh, const double* eps_r, double freq_hz,
+                        const mwi_solver_opts* opts, void* cuda_stream, mwi_problem_t* out);
+
+/* Same as mwi_assemble but eps_r [nt] (interleaved complex) is a device array. */
+mwi_status mwi_assemble_device(mwi_mesh_t mesh, const double* eps_r_dev, double freq_hz,
+                               const mwi_solver_opts* opts, void* cuda_stream, mwi_problem_t* out);
+
+/* Re-assemble and re-factorise an existing problem for new eps_r (host) at the
+ * same frequency and options, reusing its decomposition and workspaces. */
+mwi_status mwi_update_eps(mwi_problem_t prob, const double* eps_r);
+mwi_status mwi_update_eps_device(mwi_problem_t prob, const double* eps_r_dev);
+
+/* ---------------------------------------------------------------------- */
+/* Forward problems (Eq. linsys, one column per transmitter) solved together
+ * by pseudo-block FGMRES + ORAS, then S_ij = conj(q_i^T u_j) / |q_i|^2 with
+ * q_i = s_i e_{k_i} (Eq. sij for edge-current receivers).  S_out
+ * [n_rx*n_tx] interleaved complex, column-major (S_out[i + n_rx*j]).  The
+ * fields stay resident for mwi_misfit_and_gradient and mwi_fields_device.
+ * info may be NULL. */
+mwi_status mwi_forward_solve(mwi_problem_t prob, const mwi_antenna* tx, int32_t n_tx,
+                             const mwi_antenna* rx, int32_t n_rx, double* S_out,
+                             mwi_solve_info* info);
+
+/* Misfit J = 1/2 sum_ij w_ij |S_ij - S_meas_ij|^2 (Eq. defJ; w = 1 when w is
+ * NULL, Eq. defJ2's normalisation when w_ij = 1/|S_empty_ij|^2) for the S of
+ * the last mwi_forward_solve, the adjoint solve of Eq. pbadj with the same
+ * factors, and dJ_deps [nt] interleaved = dJ/dRe(eps_t) + i dJ/dIm(eps_t)
+ * (Section 5; includes the boundary term from beta = k0 sqrt(eps_t) on
+ * impedance faces).  S_meas, w: [n_rx*n_tx] column-major, host.
+ * MWI_ESTATE without a prior forward solve. */
+mwi_status mwi_misfit_and_gradient(mwi_problem_t prob, const double* S_meas, const double* w,
+                                   double* J_out, double* dJ_deps, mwi_solve_info* info);
+
+/* Same with device arrays: S_meas_dev, w_dev (nullable), dJ_deps_dev; J_out host. */
+mwi_status mwi_misfit_and_gradient_device(mwi_problem_t prob, const double* S_meas_dev,
+                                          const double* w_dev, double* J_out,
+                                          double* dJ_deps_dev, mwi_solve_info* info);
+
+/* Borrowed device view of the last fields U [n][m] (row-major: m = n_tx
+ * contiguous complex values per DOF, internal DOF order of mwi_mesh_dof_keys).
+ * which = 0 forward fields, 1 adjoint fields.  Valid until the next call on
+ * the handle. */
+mwi_status mwi_fields_device(mwi_problem_t prob, int32_t which, void** dev_ptr, int64_t* n,
+                             int64_t* m);
+
+/* Copy the last fields (as mwi_fields_device describes them) to the host
+ * array out [n*m*2] (interleaved complex, row-major [n][m]). */
+mwi_status mwi_copy_fields(mwi_problem_t prob, int32_t which, double* out);
+
+mwi_status mwi_problem_destroy(mwi_problem_t prob);
+
+/* Thread-local message for the last non-OK status of this thread. */
+const char* mwi_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Building blocks exposed for testing and measurement.  All vectors are
+ * device arrays of complex double, row-major [n][m] (m contiguous). */
+
+/* y = A x for the assembled global matrix (the complex SpMM of every FGMRES
+ * iteration). */
+mwi_status mwi_spmm_device(mwi_problem_t prob, const double* x_dev, double* y_dev, int32_t m);
+
+/* y = M^-1 x with the ORAS preconditioner of Eq. ORAS in the problem's
+ * precision (x and y in FP64; converted around the FP32 factors if MIXED). */
+mwi_status mwi_oras_apply_device(mwi_problem_t prob, const double* x_dev, double* y_dev,
+                                 int32_t m);
+
+/* Global CSR of A: row_ptr [n+1] (host), col [nnz] (host), val [2*nnz] (host). */
+mwi_status mwi_matrix_csr(mwi_problem_t prob, int64_t* nnz, int64_t* row_ptr, int32_t* col,
+                          double* val);
+
+/* Decomposition summary: part [nt] (host), and per subdomain the number of
+ * local DOFs n_local [n_sub] (host).  Either pointer may be NULL. */
+mwi_status mwi_decomposition(mwi_problem_t prob, int32_t* part, int64_t* n_local);
+
+/* Factor statistics: total factor entries, front count, largest front. */
+mwi_status mwi_factor_stats(mwi_problem_t prob, int64_t* factor_entries, int64_t* n_fronts,
+                            int64_t* max_front, double* factor_flops);
+
+/* Per-kernel timing of the last forward/adjoint solve, CUDA events on the
+ * problem's stream: ms[0] SpMM, ms[1] ORAS apply, ms[2] orthogonalisation,
+ * ms[3] other; counts[4] launches of each.  Enabled by opts.verbose >= 2. */
+mwi_status mwi_kernel_times(mwi_problem_t prob, double* ms, int64_t* counts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MWI_H */

@@ -33,7 +33,8 @@ from .fem import element_matrices, face_matrix
 
 
 def rcb_partition(xyz, tet, nparts):
-    c = xyz[np.asarray(tet)].sum(axis=1) / 4.0
+    P = xyz[np.asarray(tet)]
+    c = (((P[:, 0] + P[:, 1]) + P[:, 2]) + P[:, 3]) / 4.0
     part = np.zeros(c.shape[0], dtype=np.int64)
 
     def rec(ids, p, first):

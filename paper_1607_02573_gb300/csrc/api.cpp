@@ -1,0 +1,765 @@
+// The C ABI (include/mwi.h): handle management and the orchestration of the
+// hot path -- assemble, batched factorisation, pseudo-block FGMRES + ORAS,
+// S-parameters, misfit, adjoint solve and gradient.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+
+#include "common.h"
+#include "gmres.h"
+#include "kernels.h"
+#include "model.h"
+#include "physics.h"
+
+namespace mwi {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+static const double kPi = 3.14159265358979323846;
+static const double kC0 = 299792458.0;
+static const double kMu0 = 4.0e-7 * kPi;
+
+struct DecompEntry {
+    int n_sub, overlap, nd_leaf;
+    std::vector<int32_t> part_key;  // empty = RCB
+    Decomposition D;
+    FrontsDev F;
+    SlotMatrixDev B;
+    DevBuf<int32_t> fu_face, fu_tet;
+};
+
+template <typename T>
+static void up(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t st) { d.upload(h, st); }
+
+}  // namespace mwi
+
+using namespace mwi;
+
+struct mwi_mesh {
+    Topology T;
+    int refcount = 0;
+    cudaStream_t st = nullptr;  // internal stream for setup work
+    DevBuf<double> xyz, Kp, Mp, Bf;
+    DevBuf<int32_t> tv, tet_dofs, face_dofs, tet_faces, face_tets;
+    DevBuf<int8_t> face_lf, face_tag;
+    ElementTablesDev tabs;
+    bool have_A = false;
+    SlotMatrix A_host;
+    SlotMatrixDev A;
+    FaceUses A_fu;
+    DevBuf<int32_t> A_fu_face, A_fu_tet;
+    std::vector<std::shared_ptr<DecompEntry>> cache;
+    std::mutex mu;
+};
+
+struct mwi_problem {
+    mwi_mesh* mesh = nullptr;
+    std::shared_ptr<DecompEntry> dec;
+    cudaStream_t st = nullptr;
+    mwi_solver_opts opts;
+    double freq = 0, k0 = 0;
+    DevBuf<double2> eps, A_coef, B_coef, Aval, Bval;
+    DevBuf<float2> Aval32;
+    DevBuf<double2> ws64;
+    DevBuf<float2> ws32;
+    DevBuf<int> perturbed;
+    int n_perturbed = 0;
+    // solve state
+    DevBuf<double2> Y64, upd64;
+    DevBuf<float2> Y32, upd32;
+    Gmres<double2> outer;
+    Gmres<float2> inner;
+    DevBuf<double2> U, Lam, Brhs, R;
+    DevBuf<float2> v32, x32, r32;
+    DevBuf<double> dscratch;
+    int m_fwd = 0;
+    bool have_fwd = false, have_adj = false;
+    std::vector<int32_t> rx_dof, tx_dof;
+    std::vector<double> rx_sign, tx_sign;
+    DevBuf<int32_t> rx_dof_d, tx_dof_d;
+    DevBuf<double> rx_sign_d, tx_sign_d;
+    DevBuf<double2> cur_d, S_d, Smeas_d, r_d, grad_d;
+    DevBuf<double> w_d, J_d;
+    int n_rx = 0;
+    double setup_ms = 0;
+    int inner_total = 0;
+    // per-kernel timing (opts.verbose >= 2)
+    double t_ms[4] = {0, 0, 0, 0};
+    int64_t t_cnt[4] = {0, 0, 0, 0};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+mwi_status fail(const Error& e) {
+    set_last_error(e.what());
+    return e.status;
+}
+
+template <typename F>
+mwi_status guard(F&& f) {
+    try {
+        f();
+        return MWI_OK;
+    } catch (const Error& e) {
+        return fail(e);
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return MWI_ENOMEM;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return MWI_EINVAL;
+    }
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+mwi_solver_opts defaults(const mwi_solver_opts* o) {
+    mwi_solver_opts d;
+    std::memset(&d, 0, sizeof(d));
+    if (o) d = *o;
+    if (d.rtol <= 0) d.rtol = 1e-6;
+    if (d.max_iter <= 0) d.max_iter = 500;
+    if (d.restart <= 0) d.restart = 50;
+    if (d.n_sub <= 0) d.n_sub = 64;
+    if (d.overlap == 0) d.overlap = 1;
+    else if (d.overlap < 0) d.overlap = 0;
+    if (d.inner_iters <= 0) d.inner_iters = 30;
+    if (d.inner_rtol <= 0) d.inner_rtol = 1e-4;
+    if (d.nd_leaf <= 0) d.nd_leaf = 64;
+    return d;
+}
+
+// timed region helper: records events around fn when enabled
+template <typename Fn>
+void timed(mwi_problem* P, int slot, Fn&& fn) {
+    if (P->opts.verbose < 2) { fn(); return; }
+    MWI_CUDA(cudaEventRecord(P->ev0, P->st));
+    fn();
+    MWI_CUDA(cudaEventRecord(P->ev1, P->st));
+    MWI_CUDA(cudaEventSynchronize(P->ev1));
+    float ms = 0;
+    MWI_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+    P->t_ms[slot] += ms;
+    P->t_cnt[slot] += 1;
+}
+
+void build_mesh_device(mwi_mesh* M) {
+    Topology& T = M->T;
+    cudaStream_t st = M->st;
+    up(M->xyz, T.xyz, st);
+    up(M->tv, T.tv, st);
+    up(M->tet_dofs, T.tet_dofs, st);
+    up(M->face_dofs, T.face_dofs, st);
+    up(M->tet_faces, T.tet_faces, st);
+    up(M->face_tets, T.face_tets, st);
+    up(M->face_lf, T.face_lf, st);
+    up(M->face_tag, T.face_tag, st);
+    ElementTables tab;
+    build_element_tables(T.order, tab);
+    M->tabs.nl = tab.nl;
+    M->tabs.npack = tab.npack;
+    M->tabs.nlf = tab.nlf;
+    M->tabs.npack_f = tab.npack_f;
+    up(M->tabs.m_terms, tab.m_terms, st);
+    up(M->tabs.m_ptr, tab.m_ptr, st);
+    up(M->tabs.k_terms, tab.k_terms, st);
+    up(M->tabs.k_ptr, tab.k_ptr, st);
+    up(M->tabs.f_terms, tab.f_terms, st);
+    up(M->tabs.f_ptr, tab.f_ptr, st);
+    M->Kp.alloc((size_t)T.nt * tab.npack);
+    M->Mp.alloc((size_t)T.nt * tab.npack);
+    M->Bf.alloc((size_t)T.nf * tab.npack_f);
+    launch_elem_geom(M->xyz.p, M->tv.p, T.nt, M->tabs, M->Kp.p, M->Mp.p, st);
+    launch_face_geom(M->xyz.p, M->tv.p, M->face_tets.p, M->face_lf.p, T.nf, M->tabs, M->Bf.p, st);
+    MWI_CUDA(cudaStreamSynchronize(st));
+}
+
+void upload_slots(const SlotMatrix& S, SlotMatrixDev& D, cudaStream_t st) {
+    D.nrows = S.nrows;
+    D.nnz = (int64_t)S.col.size();
+    MWI_REQUIRE(D.nnz < ((int64_t)1 << 31), MWI_EINVAL, "matrix too large for int32 row pointers");
+    std::vector<int32_t> rp(S.row_ptr.begin(), S.row_ptr.end());
+    D.row_ptr.upload(rp, st);
+    D.col.upload(S.col, st);
+    D.slot_ptr.upload(S.slot_ptr, st);
+    D.contrib.upload(S.contrib, st);
+}
+
+void ensure_global(mwi_mesh* M) {
+    if (M->have_A) return;
+    build_global_slots(M->T, M->A_host, M->A_fu);
+    upload_slots(M->A_host, M->A, M->st);
+    up(M->A_fu_face, M->A_fu.face, M->st);
+    up(M->A_fu_tet, M->A_fu.tet, M->st);
+    MWI_CUDA(cudaStreamSynchronize(M->st));
+    M->have_A = true;
+}
+
+std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
+    std::vector<int32_t> key;
+    if (o.part) key.assign(o.part, o.part + M->T.nt);
+    for (auto& e : M->cache)
+        if (e->n_sub == o.n_sub && e->overlap == o.overlap && e->nd_leaf == o.nd_leaf && e->part_key == key)
+            return e;
+    auto E = std::make_shared<DecompEntry>();
+    E->n_sub = o.n_sub;
+    E->overlap = o.overlap;
+    E->nd_leaf = o.nd_leaf;
+    E->part_key = key;
+    build_decomposition(M->T, o.part, o.n_sub, o.overlap, o.nd_leaf, E->D);
+    Decomposition& D = E->D;
+    cudaStream_t st = M->st;
+    upload_slots(D.B, E->B, st);
+    up(E->fu_face, D.B_faces.face, st);
+    up(E->fu_tet, D.B_faces.tet, st);
+    FrontsDev& F = E->F;
+    const size_t nf = D.fronts.size();
+    F.nfronts = (int64_t)nf;
+    std::vector<int32_t> start(nf), p(nf), u(nf), parent(nf), sub(nf);
+    std::vector<int64_t> f_off(nf), u_off(nf), upd_row(nf);
+    for (size_t k = 0; k < nf; ++k) {
+        const Front& fr = D.fronts[k];
+        start[k] = fr.start; p[k] = fr.p; u[k] = fr.u; parent[k] = fr.parent; sub[k] = fr.sub;
+        f_off[k] = fr.f_off; u_off[k] = fr.u_off; upd_row[k] = fr.upd_row;
+    }
+    up(F.start, start, st); up(F.p, p, st); up(F.u, u, st); up(F.parent, parent, st); up(F.sub, sub, st);
+    up(F.f_off, f_off, st); up(F.u_off, u_off, st); up(F.upd_row, upd_row, st);
+    up(F.child_ptr, D.child_ptr, st); up(F.child, D.child, st);
+    up(F.urows, D.urows, st); up(F.urel, D.urel, st);
+    up(F.amap_front_ptr, D.amap_front_ptr, st); up(F.amap_slot, D.amap_slot, st); up(F.amap_pos, D.amap_pos, st);
+    up(F.level_fronts, D.level_fronts, st);
+    F.level_ptr = D.level_ptr;
+    const int nlev = D.n_levels;
+    F.level_pmax.assign(nlev, 0);
+    F.level_fmax.assign(nlev, 0);
+    F.level_umax.assign(nlev, 0);
+    for (int l = 0; l < nlev; ++l)
+        for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
+            const Front& fr = D.fronts[D.level_fronts[q]];
+            F.level_pmax[l] = std::max(F.level_pmax[l], fr.p);
+            F.level_fmax[l] = std::max(F.level_fmax[l], fr.p + fr.u);
+            F.level_umax[l] = std::max(F.level_umax[l], fr.u);
+        }
+    up(F.sub_off, D.sub_off, st);
+    up(F.loc2glob, D.loc2glob, st);
+    up(F.own_ptr, D.own_ptr, st);
+    up(F.own_row, D.own_row, st);
+    up(F.own_w, D.own_w, st);
+    F.nloc = D.sub_off[D.n_sub];
+    F.upd_rows = D.upd_rows;
+    F.ws_entries = D.ws_entries;
+    F.n_sub = D.n_sub;
+    MWI_CUDA(cudaStreamSynchronize(st));
+    M->cache.push_back(E);
+    return E;
+}
+
+// assemble A and B_i values for the current eps, then factorise
+void numeric_setup(mwi_problem* P) {
+    mwi_mesh* M = P->mesh;
+    const Topology& T = M->T;
+    cudaStream_t st = P->st;
+    const double t0 = now_ms();
+    P->A_coef.ensure(std::max<size_t>(1, M->A_fu.face.size()));
+    launch_face_coef(M->A_fu_tet.p, (int64_t)M->A_fu.face.size(), P->eps.p, P->k0, P->A_coef.p, st);
+    P->Aval.ensure(M->A.nnz);
+    const bool mixed = P->opts.precision == 1;
+    if (mixed) P->Aval32.ensure(M->A.nnz);
+    launch_slot_fill(M->A, M->Kp.p, M->Mp.p, M->tabs.npack, M->Bf.p, M->tabs.npack_f, M->A_fu_face.p, P->A_coef.p,
+                     P->eps.p, P->k0, P->Aval.p, mixed ? P->Aval32.p : nullptr, st);
+    DecompEntry& E = *P->dec;
+    P->B_coef.ensure(std::max<size_t>(1, E.D.B_faces.face.size()));
+    launch_face_coef(E.fu_tet.p, (int64_t)E.D.B_faces.face.size(), P->eps.p, P->k0, P->B_coef.p, st);
+    P->Bval.ensure(E.B.nnz);
+    launch_slot_fill(E.B, M->Kp.p, M->Mp.p, M->tabs.npack, M->Bf.p, M->tabs.npack_f, E.fu_face.p, P->B_coef.p,
+                     P->eps.p, P->k0, P->Bval.p, nullptr, st);
+    P->perturbed.ensure(1);
+    MWI_CUDA(cudaMemsetAsync(P->perturbed.p, 0, sizeof(int), st));
+    if (mixed) {
+        P->ws32.ensure(E.F.ws_entries);
+        factorize_fronts<float2>(E.F, P->Bval.p, P->ws32.p, P->perturbed.p, st);
+    } else {
+        P->ws64.ensure(E.F.ws_entries);
+        factorize_fronts<double2>(E.F, P->Bval.p, P->ws64.p, P->perturbed.p, st);
+    }
+    MWI_CUDA(cudaMemcpyAsync(&P->n_perturbed, P->perturbed.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MWI_CUDA(cudaStreamSynchronize(st));
+    P->setup_ms = now_ms() - t0;
+    (void)T;
+}
+
+void create_problem(mwi_mesh* M, const double* eps, bool eps_dev, double freq, const mwi_solver_opts* opts,
+                    void* stream, mwi_problem_t* out) {
+    MWI_REQUIRE(M && out, MWI_EINVAL, "null mesh or output handle");
+    MWI_REQUIRE(eps, MWI_EINVAL, "null eps_r");
+    MWI_REQUIRE(freq > 0 && std::isfinite(freq), MWI_EINVAL, "frequency must be positive");
+    std::unique_ptr<mwi_problem> P(new mwi_problem());
+    P->opts = defaults(opts);
+    MWI_REQUIRE(P->opts.precision == 0 || P->opts.precision == 1, MWI_EINVAL, "precision must be 0 or 1");
+    MWI_REQUIRE(P->opts.n_sub <= M->T.nt, MWI_EINVAL, "more subdomains than tets");
+    P->mesh = M;
+    P->st = (cudaStream_t)stream;
+    P->freq = freq;
+    P->k0 = 2.0 * kPi * freq / kC0;
+    MWI_CUDA(cudaEventCreate(&P->ev0));
+    MWI_CUDA(cudaEventCreate(&P->ev1));
+    {
+        std::lock_guard<std::mutex> lk(M->mu);
+        ensure_global(M);
+        P->dec = get_decomp(M, P->opts);
+    }
+    P->eps.alloc(M->T.nt);
+    if (eps_dev) {
+        MWI_CUDA(cudaMemcpyAsync(P->eps.p, eps, M->T.nt * sizeof(double2), cudaMemcpyDeviceToDevice, P->st));
+    } else {
+        for (int64_t t = 0; t < M->T.nt; ++t)
+            MWI_REQUIRE(std::isfinite(eps[2 * t]) && std::isfinite(eps[2 * t + 1]), MWI_EINVAL, "eps_r not finite");
+        MWI_CUDA(cudaMemcpyAsync(P->eps.p, eps, M->T.nt * sizeof(double2), cudaMemcpyHostToDevice, P->st));
+    }
+    numeric_setup(P.get());
+    M->refcount++;
+    *out = P.release();
+}
+
+void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<int32_t>& dof,
+                  std::vector<double>& sign) {
+    dof.resize(n);
+    sign.resize(n);
+    for (int k = 0; k < n; ++k) {
+        const double* pos = a[k].pos;
+        const double* dir = a[k].dir;
+        const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        MWI_REQUIRE(dn > 0 && std::isfinite(dn), MWI_EINVAL, "antenna direction must be non-zero");
+        int64_t best_v = -1;
+        double best_d = 0;
+        for (int64_t v = 0; v < T.nv; ++v) {
+            double d = 0;
+            for (int q = 0; q < 3; ++q) {
+                double x = T.xyz[3 * v + q] - pos[q];
+                d += x * x;
+            }
+            if (best_v < 0 || d < best_d) { best_v = v; best_d = d; }
+        }
+        int32_t best_e = -1;
+        double best_c = -2;
+        for (int32_t q = T.v2e_ptr[best_v]; q < T.v2e_ptr[best_v + 1]; ++q) {
+            const int32_t e = T.v2e[q];
+            const int64_t o = T.edges[2 * e] == best_v ? T.edges[2 * e + 1] : T.edges[2 * e];
+            double vec[3], nv = 0, dot = 0;
+            for (int d = 0; d < 3; ++d) {
+                vec[d] = T.xyz[3 * o + d] - T.xyz[3 * best_v + d];
+                nv += vec[d] * vec[d];
+                dot += vec[d] * dir[d];
+            }
+            const double c = dot / (std::sqrt(nv) * dn);
+            if (c > best_c) { best_c = c; best_e = e; }
+        }
+        MWI_REQUIRE(best_e >= 0, MWI_EINVAL, "antenna vertex has no edge");
+        MWI_REQUIRE(T.edge_dof[best_e] >= 0, MWI_EINVAL, "antenna falls on a PEC edge");
+        double t = 0;
+        for (int d = 0; d < 3; ++d)
+            t += (T.xyz[3 * (int64_t)T.edges[2 * best_e + 1] + d] - T.xyz[3 * (int64_t)T.edges[2 * best_e] + d]) * dir[d];
+        dof[k] = T.edge_dof[best_e];
+        sign[k] = t > 0 ? 1.0 : -1.0;
+    }
+}
+
+// solve A X = B for m columns by FGMRES; returns info
+void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
+    mwi_mesh* M = P->mesh;
+    const int64_t n = M->T.ndof;
+    const int64_t nm = n * m;
+    cudaStream_t st = P->st;
+    const mwi_solver_opts& o = P->opts;
+    const bool mixed = o.precision == 1;
+    DecompEntry& E = *P->dec;
+    const int restart = std::min(o.restart, std::max(1, o.max_iter));
+    P->outer.reserve(n, m, restart);
+    P->R.ensure(nm);
+    P->dscratch.ensure(4 * (size_t)m);
+    double* b2 = P->dscratch.p;
+    double* tol = P->dscratch.p + m;
+    double* bnorm = P->dscratch.p + 2 * m;
+    double* r2 = P->dscratch.p + 3 * m;
+    // local solve buffers
+    if (mixed) {
+        P->Y32.ensure((size_t)E.F.nloc * m);
+        P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+        P->inner.reserve(n, m, std::max(1, o.inner_iters));
+        P->v32.ensure(nm);
+        P->x32.ensure(nm);
+    } else {
+        P->Y64.ensure((size_t)E.F.nloc * m);
+        P->upd64.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+    }
+    auto A64 = [&](const double2* x, double2* y) {
+        timed(P, 0, [&] { spmm<double2>(n, M->A.row_ptr.p, M->A.col.p, P->Aval.p, x, y, m, st); });
+    };
+    auto A32 = [&](const float2* x, float2* y) {
+        timed(P, 0, [&] { spmm<float2>(n, M->A.row_ptr.p, M->A.col.p, P->Aval32.p, x, y, m, st); });
+    };
+    auto M32 = [&](const float2* x, float2* y) {
+        timed(P, 1, [&] {
+            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->upd32.p, st, x, y);
+        });
+    };
+    auto M64 = [&](const double2* x, double2* y) {
+        if (!mixed) {
+            timed(P, 1, [&] { oras_apply<double2>(E.F, P->ws64.p, x, y, m, P->Y64.p, P->upd64.p, st); });
+            return;
+        }
+        // inner GMRES in complex FP32 on A z = x, preconditioned by the FP32 ORAS
+        convert_c128_to_c64(nm, x, P->v32.p, st);
+        MWI_CUDA(cudaMemsetAsync(P->x32.p, 0, nm * sizeof(float2), st));
+        double* vb2 = P->inner.dvec.p + 5 * m;
+        double* tin = P->inner.dvec.p + 6 * m;
+        double* vn = P->inner.dvec.p + 7 * m;
+        P->inner.column_norms2(P->v32.p, vb2, st);
+        tolerances(m, vb2, o.inner_rtol, tin, vn, st);
+        int used = 0;
+        P->inner.cycle(A32, M32, P->v32.p, P->x32.p, tin, std::max(1, o.inner_iters), st, nullptr, &used);
+        P->inner_total += used;
+        convert_c64_to_c128(nm, P->x32.p, y, st);
+    };
+
+    const double t0 = now_ms();
+    P->inner_total = 0;
+    P->outer.column_norms2(B, b2, st);
+    tolerances(m, b2, o.rtol, tol, bnorm, st);
+    std::vector<double> bn(m), rn(m);
+    MWI_CUDA(cudaMemcpyAsync(bn.data(), bnorm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MWI_CUDA(cudaMemsetAsync(X, 0, nm * sizeof(double2), st));
+    MWI_CUDA(cudaMemcpyAsync(P->R.p, B, nm * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    int total = 0;
+    bool done = false;
+    while (!done) {
+        int used = 0;
+        P->outer.cycle(A64, M64, P->R.p, X, tol, std::min(restart, o.max_iter - total), st, nullptr, &used);
+        total += used;
+        // true FP64 residual
+        A64(X, P->R.p);
+        residual_c128(nm, B, P->R.p, st);
+        P->outer.column_norms2(P->R.p, r2, st);
+        MWI_CUDA(cudaMemcpyAsync(rn.data(), r2, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+        done = true;
+        for (int c = 0; c < m; ++c)
+            if (bn[c] > 0 && std::sqrt(std::max(rn[c], 0.0)) > o.rtol * bn[c]) done = false;
+        if (total >= o.max_iter || used == 0) break;
+    }
+    int nconv = 0;
+    double rmax = 0;
+    for (int c = 0; c < m; ++c) {
+        double rel = bn[c] > 0 ? std::sqrt(std::max(rn[c], 0.0)) / bn[c] : 0.0;
+        rmax = std::max(rmax, rel);
+        if (rel <= o.rtol) nconv++;
+    }
+    if (info) {
+        info->iters_max = total;
+        info->inner_total = P->inner_total;
+        info->n_converged = nconv;
+        info->n_perturbed = P->n_perturbed;
+        info->resid_max = rmax;
+        info->setup_ms = P->setup_ms;
+        info->solve_ms = now_ms() - t0;
+    }
+    if (nconv < m) throw Error(MWI_ENOTCONV, "FGMRES did not reach rtol on every column");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mwi_last_error(void) { return g_last_error.c_str(); }
+
+mwi_status mwi_mesh_create(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt, const int32_t* bface_tag,
+                           int32_t order, mwi_mesh_t* out) {
+    return guard([&] {
+        MWI_REQUIRE(xyz && tet && bface_tag && out, MWI_EINVAL, "null argument");
+        std::unique_ptr<mwi_mesh> M(new mwi_mesh());
+        build_topology(M->T, xyz, nv, tet, nt, bface_tag, order);
+        MWI_CUDA(cudaStreamCreateWithFlags(&M->st, cudaStreamNonBlocking));
+        build_mesh_device(M.get());
+        *out = M.release();
+    });
+}
+
+mwi_status mwi_mesh_ndof(mwi_mesh_t mesh, int64_t* ndof) {
+    return guard([&] {
+        MWI_REQUIRE(mesh && ndof, MWI_EINVAL, "null argument");
+        *ndof = mesh->T.ndof;
+    });
+}
+
+mwi_status mwi_mesh_dof_keys(mwi_mesh_t mesh, int32_t* kind, int64_t* verts) {
+    return guard([&] {
+        MWI_REQUIRE(mesh, MWI_EINVAL, "null mesh");
+        if (kind) std::copy(mesh->T.dof_kind.begin(), mesh->T.dof_kind.end(), kind);
+        if (verts) std::copy(mesh->T.dof_verts.begin(), mesh->T.dof_verts.end(), verts);
+    });
+}
+
+mwi_status mwi_mesh_destroy(mwi_mesh_t mesh) {
+    return guard([&] {
+        if (!mesh) return;
+        MWI_REQUIRE(mesh->refcount == 0, MWI_ESTATE, "mesh is still referenced by a problem");
+        if (mesh->st) cudaStreamDestroy(mesh->st);
+        delete mesh;
+    });
+}
+
+mwi_status mwi_assemble(mwi_mesh_t mesh, const double* eps_r, double freq_hz, const mwi_solver_opts* opts,
+                        void* cuda_stream, mwi_problem_t* out) {
+    return guard([&] { create_problem(mesh, eps_r, false, freq_hz, opts, cuda_stream, out); });
+}
+
+mwi_status mwi_assemble_device(mwi_mesh_t mesh, const double* eps_r_dev, double freq_hz,
+                               const mwi_solver_opts* opts, void* cuda_stream, mwi_problem_t* out) {
+    return guard([&] { create_problem(mesh, eps_r_dev, true, freq_hz, opts, cuda_stream, out); });
+}
+
+static void update_eps(mwi_problem_t P, const double* eps, bool dev) {
+    MWI_REQUIRE(P && eps, MWI_EINVAL, "null argument");
+    const int64_t nt = P->mesh->T.nt;
+    if (!dev)
+        for (int64_t t = 0; t < nt; ++t)
+            MWI_REQUIRE(std::isfinite(eps[2 * t]) && std::isfinite(eps[2 * t + 1]), MWI_EINVAL, "eps_r not finite");
+    MWI_CUDA(cudaMemcpyAsync(P->eps.p, eps, nt * sizeof(double2),
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, P->st));
+    numeric_setup(P);
+    P->have_fwd = false;
+    P->have_adj = false;
+}
+
+mwi_status mwi_update_eps(mwi_problem_t prob, const double* eps_r) {
+    return guard([&] { update_eps(prob, eps_r, false); });
+}
+mwi_status mwi_update_eps_device(mwi_problem_t prob, const double* eps_r_dev) {
+    return guard([&] { update_eps(prob, eps_r_dev, true); });
+}
+
+mwi_status mwi_forward_solve(mwi_problem_t P, const mwi_antenna* tx, int32_t n_tx, const mwi_antenna* rx,
+                             int32_t n_rx, double* S_out, mwi_solve_info* info) {
+    mwi_status status = MWI_OK;
+    mwi_status g = guard([&] {
+        MWI_REQUIRE(P && tx && rx && S_out, MWI_EINVAL, "null argument");
+        MWI_REQUIRE(n_tx >= 1 && n_rx >= 1 && n_tx <= 4096 && n_rx <= 4096, MWI_EINVAL, "bad antenna count");
+        const Topology& T = P->mesh->T;
+        cudaStream_t st = P->st;
+        map_antennas(T, tx, n_tx, P->tx_dof, P->tx_sign);
+        map_antennas(T, rx, n_rx, P->rx_dof, P->rx_sign);
+        const int m = n_tx;
+        const int64_t nm = T.ndof * (int64_t)m;
+        P->tx_dof_d.upload(P->tx_dof, st);
+        P->tx_sign_d.upload(P->tx_sign, st);
+        P->rx_dof_d.upload(P->rx_dof, st);
+        P->rx_sign_d.upload(P->rx_sign, st);
+        std::vector<double2> cur(m);
+        for (int j = 0; j < m; ++j) cur[j] = make_double2(tx[j].re_I, tx[j].im_I);
+        P->cur_d.upload(cur, st);
+        P->Brhs.ensure(nm);
+        P->U.ensure(nm);
+        MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));
+        launch_rhs(m, P->tx_dof_d.p, P->tx_sign_d.p, P->cur_d.p, 2.0 * kPi * P->freq * kMu0, P->Brhs.p, st);
+        for (int k = 0; k < 4; ++k) { P->t_ms[k] = 0; P->t_cnt[k] = 0; }
+        P->m_fwd = m;
+        P->n_rx = n_rx;
+        try {
+            solve_block(P, P->Brhs.p, P->U.p, m, info);
+        } catch (const Error& e) {
+            if (e.status != MWI_ENOTCONV) throw;
+            status = MWI_ENOTCONV;
+            set_last_error(e.what());
+        }
+        P->S_d.ensure((size_t)n_rx * m);
+        launch_s_extract(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->U.p, P->S_d.p, st);
+        MWI_CUDA(cudaMemcpyAsync(S_out, P->S_d.p, (size_t)n_rx * m * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+        P->have_fwd = true;
+        P->have_adj = false;
+    });
+    return g != MWI_OK ? g : status;
+}
+
+static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const double* w, double* J_out,
+                                   double* dJ, mwi_solve_info* info, bool dev) {
+    mwi_status status = MWI_OK;
+    mwi_status g = guard([&] {
+        MWI_REQUIRE(P && S_meas && J_out && dJ, MWI_EINVAL, "null argument");
+        MWI_REQUIRE(P->have_fwd, MWI_ESTATE, "misfit_and_gradient needs a prior forward_solve");
+        const Topology& T = P->mesh->T;
+        cudaStream_t st = P->st;
+        const int m = P->m_fwd, n_rx = P->n_rx;
+        const int cnt = n_rx * m;
+        const int64_t nm = T.ndof * (int64_t)m;
+        const auto kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        P->Smeas_d.ensure(cnt);
+        P->r_d.ensure(cnt);
+        P->J_d.ensure(1);
+        MWI_CUDA(cudaMemcpyAsync(P->Smeas_d.p, S_meas, cnt * sizeof(double2), kind, st));
+        const double* wd = nullptr;
+        if (w) {
+            P->w_d.ensure(cnt);
+            MWI_CUDA(cudaMemcpyAsync(P->w_d.p, w, cnt * sizeof(double), kind, st));
+            wd = P->w_d.p;
+        }
+        launch_misfit(cnt, P->S_d.p, P->Smeas_d.p, wd, P->r_d.p, P->J_d.p, st);
+        P->Brhs.ensure(nm);
+        MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));
+        launch_adjoint_rhs(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->r_d.p, wd, P->Brhs.p, st);
+        P->Lam.ensure(nm);
+        try {
+            solve_block(P, P->Brhs.p, P->Lam.p, m, info);
+        } catch (const Error& e) {
+            if (e.status != MWI_ENOTCONV) throw;
+            status = MWI_ENOTCONV;
+            set_last_error(e.what());
+        }
+        double2* out = dev ? reinterpret_cast<double2*>(dJ) : nullptr;
+        if (!dev) {
+            P->grad_d.ensure(T.nt);
+            out = P->grad_d.p;
+        }
+        mwi_mesh* M = P->mesh;
+        launch_gradient(T.order, T.nt, m, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p, M->face_dofs.p, M->Mp.p,
+                        M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, out, st);
+        MWI_CUDA(cudaMemcpyAsync(J_out, P->J_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (!dev)
+            MWI_CUDA(cudaMemcpyAsync(dJ, P->grad_d.p, T.nt * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+        P->have_adj = true;
+    });
+    return g != MWI_OK ? g : status;
+}
+
+mwi_status mwi_misfit_and_gradient(mwi_problem_t prob, const double* S_meas, const double* w, double* J_out,
+                                   double* dJ_deps, mwi_solve_info* info) {
+    return misfit_grad_impl(prob, S_meas, w, J_out, dJ_deps, info, false);
+}
+
+mwi_status mwi_misfit_and_gradient_device(mwi_problem_t prob, const double* S_meas_dev, const double* w_dev,
+                                          double* J_out, double* dJ_deps_dev, mwi_solve_info* info) {
+    return misfit_grad_impl(prob, S_meas_dev, w_dev, J_out, dJ_deps_dev, info, true);
+}
+
+mwi_status mwi_fields_device(mwi_problem_t P, int32_t which, void** dev_ptr, int64_t* n, int64_t* m) {
+    return guard([&] {
+        MWI_REQUIRE(P && dev_ptr, MWI_EINVAL, "null argument");
+        MWI_REQUIRE(which == 0 || which == 1, MWI_EINVAL, "which must be 0 or 1");
+        MWI_REQUIRE(which == 0 ? P->have_fwd : P->have_adj, MWI_ESTATE, "no fields of that kind yet");
+        *dev_ptr = which == 0 ? (void*)P->U.p : (void*)P->Lam.p;
+        if (n) *n = P->mesh->T.ndof;
+        if (m) *m = P->m_fwd;
+    });
+}
+
+mwi_status mwi_copy_fields(mwi_problem_t P, int32_t which, double* out) {
+    return guard([&] {
+        MWI_REQUIRE(P && out, MWI_EINVAL, "null argument");
+        MWI_REQUIRE(which == 0 || which == 1, MWI_EINVAL, "which must be 0 or 1");
+        MWI_REQUIRE(which == 0 ? P->have_fwd : P->have_adj, MWI_ESTATE, "no fields of that kind yet");
+        const double2* src = which == 0 ? P->U.p : P->Lam.p;
+        MWI_CUDA(cudaMemcpyAsync(out, src, (size_t)P->mesh->T.ndof * P->m_fwd * sizeof(double2),
+                                 cudaMemcpyDeviceToHost, P->st));
+        MWI_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+mwi_status mwi_problem_destroy(mwi_problem_t P) {
+    return guard([&] {
+        if (!P) return;
+        if (P->st) cudaStreamSynchronize(P->st);
+        if (P->ev0) cudaEventDestroy(P->ev0);
+        if (P->ev1) cudaEventDestroy(P->ev1);
+        P->mesh->refcount--;
+        delete P;
+    });
+}
+
+mwi_status mwi_spmm_device(mwi_problem_t P, const double* x_dev, double* y_dev, int32_t m) {
+    return guard([&] {
+        MWI_REQUIRE(P && x_dev && y_dev && m >= 1, MWI_EINVAL, "bad argument");
+        mwi_mesh* M = P->mesh;
+        spmm<double2>(M->T.ndof, M->A.row_ptr.p, M->A.col.p, P->Aval.p, (const double2*)x_dev, (double2*)y_dev, m,
+                      P->st);
+        MWI_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y_dev, int32_t m) {
+    return guard([&] {
+        MWI_REQUIRE(P && x_dev && y_dev && m >= 1, MWI_EINVAL, "bad argument");
+        DecompEntry& E = *P->dec;
+        const int64_t n = P->mesh->T.ndof;
+        if (P->opts.precision == 1) {
+            P->Y32.ensure((size_t)E.F.nloc * m);
+            P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+            P->v32.ensure(n * m);
+            P->x32.ensure(n * m);
+            convert_c128_to_c64(n * m, (const double2*)x_dev, P->v32.p, P->st);
+            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->upd32.p, P->st, P->v32.p, P->x32.p);
+            convert_c64_to_c128(n * m, P->x32.p, (double2*)y_dev, P->st);
+        } else {
+            P->Y64.ensure((size_t)E.F.nloc * m);
+            P->upd64.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+            oras_apply<double2>(E.F, P->ws64.p, (const double2*)x_dev, (double2*)y_dev, m, P->Y64.p, P->upd64.p,
+                                P->st);
+        }
+        MWI_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+mwi_status mwi_matrix_csr(mwi_problem_t P, int64_t* nnz, int64_t* row_ptr, int32_t* col, double* val) {
+    return guard([&] {
+        MWI_REQUIRE(P && nnz, MWI_EINVAL, "null argument");
+        mwi_mesh* M = P->mesh;
+        *nnz = M->A.nnz;
+        if (row_ptr) std::copy(M->A_host.row_ptr.begin(), M->A_host.row_ptr.end(), row_ptr);
+        if (col) std::copy(M->A_host.col.begin(), M->A_host.col.end(), col);
+        if (val) {
+            MWI_CUDA(cudaMemcpyAsync(val, P->Aval.p, M->A.nnz * sizeof(double2), cudaMemcpyDeviceToHost, P->st));
+            MWI_CUDA(cudaStreamSynchronize(P->st));
+        }
+    });
+}
+
+mwi_status mwi_decomposition(mwi_problem_t P, int32_t* part, int64_t* n_local) {
+    return guard([&] {
+        MWI_REQUIRE(P, MWI_EINVAL, "null problem");
+        const Decomposition& D = P->dec->D;
+        if (part) std::copy(D.part.begin(), D.part.end(), part);
+        if (n_local)
+            for (int i = 0; i < D.n_sub; ++i) n_local[i] = D.sub_off[i + 1] - D.sub_off[i];
+    });
+}
+
+mwi_status mwi_factor_stats(mwi_problem_t P, int64_t* factor_entries, int64_t* n_fronts, int64_t* max_front,
+                            double* factor_flops) {
+    return guard([&] {
+        MWI_REQUIRE(P, MWI_EINVAL, "null problem");
+        const Decomposition& D = P->dec->D;
+        if (factor_entries) *factor_entries = D.factor_entries;
+        if (n_fronts) *n_fronts = (int64_t)D.fronts.size();
+        if (max_front) *max_front = D.max_front;
+        if (factor_flops) *factor_flops = D.factor_flops;
+    });
+}
+
+mwi_status mwi_kernel_times(mwi_problem_t P, double* ms, int64_t* counts) {
+    return guard([&] {
+        MWI_REQUIRE(P, MWI_EINVAL, "null problem");
+        for (int k = 0; k < 4; ++k) {
+            if (ms) ms[k] = P->t_ms[k];
+            if (counts) counts[k] = P->t_cnt[k];
+        }
+    });
+}
+
+}  // extern "C"

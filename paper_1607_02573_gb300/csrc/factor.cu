@@ -1,0 +1,249 @@
+// Batched multifrontal LDL^T factorisation of every subdomain operator B_i
+// (the local solves of Eq. ORAS; the paper uses PARDISO/MUMPS per MPI rank,
+// here all subdomains are one batch on one GPU).
+//
+// B_i is complex symmetric (the form of Eq. pbdirectvarf is bilinear), so
+// B_i = L D L^T without conjugation.  Pivoting is static: Im(B_i) is positive
+// definite for a lossy medium (Im eps < 0), which makes every leading minor
+// non-zero; a pivot that is zero or not finite is replaced and counted.
+//
+// The fronts of one assembly-tree depth are processed together, deepest
+// depth first: assemble (entries of B_i, then extend-add of the children's
+// Schur complements), then a blocked right-looking partial factorisation of
+// the p pivot columns (panel kernel + trailing-update kernel) that leaves the
+// Schur complement in the front's trailing block for the parent.
+// Fronts are dense, column-major f x f, lower triangle used; the first p
+// columns hold L (unit diagonal implied) with D on the diagonal.
+#include <algorithm>
+
+#include "common.h"
+#include "kernels.h"
+
+namespace mwi {
+
+template <typename C> __device__ __forceinline__ C from_d2(double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+template <typename C>
+__global__ void front_assemble_kernel(const int32_t* __restrict__ level_fronts, int lo,
+                                      const int64_t* __restrict__ amap_front_ptr,
+                                      const int64_t* __restrict__ amap_slot, const int64_t* __restrict__ amap_pos,
+                                      const double2* __restrict__ B, C* __restrict__ ws) {
+    const int s = level_fronts[lo + blockIdx.x];
+    for (int64_t q = amap_front_ptr[s] + threadIdx.x; q < amap_front_ptr[s + 1]; q += blockDim.x)
+        ws[amap_pos[q]] = from_d2<C>(B[amap_slot[q]]);
+}
+
+// child ci of every front of the level: parent[urel[b], urel[a]] += child[p_c + a, p_c + b], a >= b
+template <typename C>
+__global__ void extend_add_kernel(const int32_t* __restrict__ level_fronts, int lo, int ci,
+                                  const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child,
+                                  const int32_t* __restrict__ P, const int32_t* __restrict__ U,
+                                  const int64_t* __restrict__ f_off, const int64_t* __restrict__ u_off,
+                                  const int32_t* __restrict__ urel, C* __restrict__ ws) {
+    const int s = level_fronts[lo + blockIdx.y];
+    if (child_ptr[s] + ci >= child_ptr[s + 1]) return;
+    const int c = child[child_ptr[s] + ci];
+    const int pc = P[c], uc = U[c];
+    const int64_t fc = (int64_t)pc + uc;
+    const int b = blockIdx.x * blockDim.y + threadIdx.y;
+    if (b >= uc) return;
+    const int64_t fs = (int64_t)P[s] + U[s];
+    const int32_t* rel = urel + u_off[c];
+    const C* src = ws + f_off[c] + (pc + b) * fc + pc;
+    C* dst = ws + f_off[s] + (int64_t)rel[b] * fs;
+    for (int a = b + threadIdx.x; a < uc; a += blockDim.x) {
+        C v = src[a];
+        C& d = dst[rel[a]];
+        d.x += v.x;
+        d.y += v.y;
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ bool bad_pivot(C d) {
+    typename real_of<C>::type a = d.x * d.x + d.y * d.y;
+    return !(a > (typename real_of<C>::type)0) || !isfinite(a);
+}
+
+// Panel k..k+nb of every front of the level: factor the diagonal block in
+// shared memory, then L_i = x_i L11^{-T} D^{-1} for every row below.
+template <typename C, int NB>
+__global__ void __launch_bounds__(256) panel_kernel(const int32_t* __restrict__ level_fronts, int lo, int k,
+                                                    const int32_t* __restrict__ P, const int32_t* __restrict__ U,
+                                                    const int64_t* __restrict__ f_off, C* __restrict__ ws,
+                                                    int* __restrict__ perturbed) {
+    const int s = level_fronts[lo + blockIdx.x];
+    const int p = P[s];
+    if (k >= p) return;
+    const int64_t f = (int64_t)p + U[s];
+    const int nb = min(NB, p - k);
+    C* F = ws + f_off[s];
+    __shared__ C Dg[NB][NB + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        int r = e % NB, c = e / NB;
+        Dg[r][c] = (r < nb && c < nb && r >= c) ? F[(int64_t)(k + c) * f + k + r] : czero<C>();
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        C d = Dg[j][j];
+        if (bad_pivot(d)) {
+            __syncthreads();
+            if (tid == 0) {
+                Dg[j][j] = cmake<C>(1, 0);
+                atomicAdd(perturbed, 1);
+            }
+            __syncthreads();
+            d = Dg[j][j];
+        }
+        C dinv = crecip(d);
+        // l_rj = a_rj / d_j for r > j (each thread one r)
+        if (tid > j && tid < nb) Dg[tid][j] = cmul(Dg[tid][j], dinv);
+        __syncthreads();
+        for (int e = tid; e < nb * nb; e += blockDim.x) {
+            int r = e % nb, c = e / nb;
+            if (c > j && r >= c) Dg[r][c] = csub(Dg[r][c], cmul(cmul(Dg[r][j], d), Dg[c][j]));
+        }
+        __syncthreads();
+    }
+    // rows below the diagonal block
+    for (int64_t i = k + nb + tid; i < f; i += blockDim.x) {
+        C w[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) w[j] = j < nb ? F[(int64_t)(k + j) * f + i] : czero<C>();
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (j >= nb) break;
+            C acc = w[j];
+#pragma unroll
+            for (int c = 0; c < j; ++c) acc = cfms(w[c], Dg[j][c], acc);
+            w[j] = acc;  // = (L_i D)_j
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j < nb) F[(int64_t)(k + j) * f + i] = cmul(w[j], crecip(Dg[j][j]));
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        int r = e % nb, c = e / nb;
+        if (r >= c) F[(int64_t)(k + c) * f + k + r] = Dg[r][c];
+    }
+}
+
+// Trailing update of the lower triangle: F[i][c] -= sum_j L[i][j] d_j L[c][j],
+// rows/cols in [k + nb, f).  TILE x TILE output tile per block, 256 threads.
+template <typename C, int TILE, int NB>
+__global__ void __launch_bounds__(256) update_kernel(const int32_t* __restrict__ level_fronts, int lo, int k,
+                                                     const int32_t* __restrict__ P, const int32_t* __restrict__ U,
+                                                     const int64_t* __restrict__ f_off, C* __restrict__ ws) {
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bj > bi) return;
+    const int s = level_fronts[lo + blockIdx.z];
+    const int p = P[s];
+    if (k >= p) return;
+    const int64_t f = (int64_t)p + U[s];
+    const int nb = min(NB, p - k);
+    const int64_t r0 = k + nb;
+    const int64_t nrem = f - r0;
+    if ((int64_t)bi * TILE >= nrem) return;
+    C* F = ws + f_off[s];
+    constexpr int MT = TILE / 16;
+    __shared__ C As[NB][TILE + 1];
+    __shared__ C Bs[NB][TILE + 1];
+    const int tid = threadIdx.x;
+    const int64_t rowA = r0 + (int64_t)bi * TILE, rowB = r0 + (int64_t)bj * TILE;
+    for (int e = tid; e < NB * TILE; e += 256) {
+        int ii = e % TILE, j = e / TILE;
+        C a = czero<C>(), b = czero<C>();
+        if (j < nb) {
+            C d = F[(int64_t)(k + j) * f + k + j];
+            if (rowA + ii < f) a = cmul(F[(int64_t)(k + j) * f + rowA + ii], d);
+            if (rowB + ii < f) b = F[(int64_t)(k + j) * f + rowB + ii];
+        }
+        As[j][ii] = a;
+        Bs[j][ii] = b;
+    }
+    __syncthreads();
+    const int tx = tid % 16, ty = tid / 16;
+    C acc[MT][MT];
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int b = 0; b < MT; ++b) acc[a][b] = czero<C>();
+#pragma unroll 4
+    for (int j = 0; j < NB; ++j) {
+        C av[MT], bv[MT];
+#pragma unroll
+        for (int a = 0; a < MT; ++a) av[a] = As[j][tx + 16 * a];
+#pragma unroll
+        for (int b = 0; b < MT; ++b) bv[b] = Bs[j][ty + 16 * b];
+#pragma unroll
+        for (int a = 0; a < MT; ++a)
+#pragma unroll
+            for (int b = 0; b < MT; ++b) acc[a][b] = cfma(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int b = 0; b < MT; ++b) {
+        const int64_t col = rowB + ty + 16 * b;
+        if (col >= f) continue;
+#pragma unroll
+        for (int a = 0; a < MT; ++a) {
+            const int64_t row = rowA + tx + 16 * a;
+            if (row < f && row >= col) {
+                C& dst = F[col * f + row];
+                dst = csub(dst, acc[a][b]);
+            }
+        }
+    }
+}
+
+template <typename C> struct FactorCfg;
+template <> struct FactorCfg<float2> { static constexpr int NB = 32; static constexpr int TILE = 64; };
+template <> struct FactorCfg<double2> { static constexpr int NB = 16; static constexpr int TILE = 32; };
+
+template <typename C>
+void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, int* perturbed, cudaStream_t st) {
+    constexpr int NB = FactorCfg<C>::NB, TILE = FactorCfg<C>::TILE;
+    MWI_CUDA(cudaMemsetAsync(ws, 0, (size_t)F.ws_entries * sizeof(C), st));
+    const int nlev = (int)F.level_ptr.size() - 1;
+    for (int l = 0; l < nlev; ++l) {
+        const int lo0 = F.level_ptr[l], hi = F.level_ptr[l + 1];
+        for (int lo = lo0; lo < hi; lo += 65535) {
+            const int nf = std::min(65535, hi - lo);
+            front_assemble_kernel<C><<<nf, 256, 0, st>>>(F.level_fronts.p, lo, F.amap_front_ptr.p, F.amap_slot.p,
+                                                         F.amap_pos.p, Bvals, ws);
+            MWI_CHECK_LAUNCH();
+            // children sit one level deeper; their maximum update size bounds the grid
+            const int umax_child = l > 0 ? F.level_umax[l - 1] : 0;
+            if (umax_child > 0) {
+                dim3 blk(64, 4);
+                dim3 grd((umax_child + 3) / 4, nf);
+                for (int ci = 0; ci < 2; ++ci) {
+                    extend_add_kernel<C><<<grd, blk, 0, st>>>(F.level_fronts.p, lo, ci, F.child_ptr.p, F.child.p,
+                                                              F.p.p, F.u.p, F.f_off.p, F.u_off.p, F.urel.p, ws);
+                    MWI_CHECK_LAUNCH();
+                }
+            }
+            const int pmax = F.level_pmax[l];
+            const int fmax = F.level_fmax[l];
+            for (int k = 0; k < pmax; k += NB) {
+                panel_kernel<C, NB><<<nf, 256, 0, st>>>(F.level_fronts.p, lo, k, F.p.p, F.u.p, F.f_off.p, ws,
+                                                        perturbed);
+                MWI_CHECK_LAUNCH();
+                const int nrem = fmax - k - 1;
+                if (nrem <= 0) continue;
+                const int T = (nrem + TILE - 1) / TILE;
+                update_kernel<C, TILE, NB><<<dim3(T, T, nf), 256, 0, st>>>(F.level_fronts.p, lo, k, F.p.p, F.u.p,
+                                                                           F.f_off.p, ws);
+                MWI_CHECK_LAUNCH();
+            }
+        }
+    }
+}
+
+template void factorize_fronts<float2>(const FrontsDev&, const double2*, float2*, int*, cudaStream_t);
+template void factorize_fronts<double2>(const FrontsDev&, const double2*, double2*, int*, cudaStream_t);
+
+}  // namespace mwi

@@ -1,0 +1,92 @@
+// Declarations of the device-side data structures and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.h"
+
+namespace mwi {
+
+// closed-form element integral tables (see assemble.cu)
+struct MTerm { double c; int8_t a, b, pad[6]; };
+struct KTerm { double c; int8_t k, gp, l, gq, pad[4]; };
+struct FTerm { double c; int8_t a, b, d, pad[5]; };
+
+struct ElementTables {
+    int nl = 0, npack = 0, nlf = 0, npack_f = 0;
+    std::vector<MTerm> m_terms;
+    std::vector<int32_t> m_ptr;
+    std::vector<KTerm> k_terms;
+    std::vector<int32_t> k_ptr;
+    std::vector<FTerm> f_terms;   // 4 local faces x npack_f pairs
+    std::vector<int32_t> f_ptr;
+};
+
+struct ElementTablesDev {
+    int nl = 0, npack = 0, nlf = 0, npack_f = 0;
+    DevBuf<MTerm> m_terms;
+    DevBuf<int32_t> m_ptr;
+    DevBuf<KTerm> k_terms;
+    DevBuf<int32_t> k_ptr;
+    DevBuf<FTerm> f_terms;
+    DevBuf<int32_t> f_ptr;
+};
+
+void build_element_tables(int order, ElementTables& tab);
+
+struct SlotMatrixDev {
+    int64_t nrows = 0, nnz = 0;
+    DevBuf<int32_t> row_ptr;   // int32 row pointers (nnz < 2^31)
+    DevBuf<int32_t> col;
+    DevBuf<int64_t> slot_ptr;
+    DevBuf<int64_t> contrib;
+};
+
+void launch_elem_geom(const double* xyz, const int32_t* tv, int64_t nt, const ElementTablesDev& tab,
+                      double* K, double* M, cudaStream_t st);
+void launch_face_geom(const double* xyz, const int32_t* tv, const int32_t* face_tets, const int8_t* face_lf,
+                      int64_t nf, const ElementTablesDev& tab, double* Bf, cudaStream_t st);
+void launch_face_coef(const int32_t* fu_tet, int64_t nfu, const double2* eps, double k0, double2* coef,
+                      cudaStream_t st);
+void launch_slot_fill(const SlotMatrixDev& S, const double* K, const double* M, int npack, const double* Bf,
+                      int npack_f, const int32_t* fu_face, const double2* fu_coef, const double2* eps, double k0,
+                      double2* out64, float2* out32, cudaStream_t st);
+
+// ---- multifrontal factorisation and ORAS application (factor.cu, oras.cu)
+struct FrontsDev {
+    int64_t nfronts = 0;
+    DevBuf<int32_t> start, p, u, parent, sub;
+    DevBuf<int64_t> f_off, u_off, upd_row;
+    DevBuf<int32_t> child_ptr, child;
+    DevBuf<int32_t> urows, urel;
+    DevBuf<int64_t> amap_front_ptr, amap_slot, amap_pos;
+    DevBuf<int32_t> level_fronts;
+    std::vector<int32_t> level_ptr;   // host copy
+    std::vector<int32_t> level_pmax;  // host: max p per level
+    std::vector<int32_t> level_fmax;  // host: max front size per level
+    std::vector<int32_t> level_umax;
+    DevBuf<int64_t> sub_off;
+    DevBuf<int32_t> loc2glob;
+    DevBuf<int64_t> own_ptr;
+    DevBuf<int32_t> own_row;
+    DevBuf<double> own_w;
+    int64_t nloc = 0, upd_rows = 0, ws_entries = 0;
+    int n_sub = 0;
+};
+
+template <typename C>
+void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, int* perturbed, cudaStream_t st);
+
+template <typename C>
+void oras_apply(const FrontsDev& F, const C* ws, const double2* x, double2* y, int m, C* Y, C* upd,
+                cudaStream_t st, const float2* x32 = nullptr, float2* y32 = nullptr);
+
+// ---- Krylov building blocks (krylov.cu)
+template <typename C>
+void spmm(int64_t n, const int32_t* row_ptr, const int32_t* col, const C* val, const C* x, C* y, int m,
+          cudaStream_t st);
+
+}  // namespace mwi

@@ -1,0 +1,285 @@
+"""ctypes binding of libmwi.so: the C entry points under their C names, plus
+two small handle classes that marshal NumPy / torch arrays.
+
+Only argument marshalling happens here; every step of the computation runs
+in the CUDA library.  Importing this module raises if the library has not
+been built (``python -m paper_1607_02573_gb300.build``).
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmwi.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_1607_02573_gb300.build")
+_lib = C.CDLL(LIB_PATH)
+
+MWI_OK, MWI_EINVAL, MWI_ENOMEM, MWI_ENOTCONV, MWI_ECUDA, MWI_ETIMEOUT, MWI_ESTATE, MWI_ESINGULAR = range(8)
+STATUS_NAMES = ["MWI_OK", "MWI_EINVAL", "MWI_ENOMEM", "MWI_ENOTCONV", "MWI_ECUDA", "MWI_ETIMEOUT",
+                "MWI_ESTATE", "MWI_ESINGULAR"]
+
+
+class MwiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class mwi_antenna(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("dir", C.c_double * 3), ("re_I", C.c_double), ("im_I", C.c_double)]
+
+
+class mwi_solver_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("restart", C.c_int32), ("n_sub", C.c_int32),
+                ("overlap", C.c_int32), ("precision", C.c_int32), ("inner_iters", C.c_int32),
+                ("inner_rtol", C.c_double), ("nd_leaf", C.c_int32), ("verbose", C.c_int32),
+                ("part", C.POINTER(C.c_int32))]
+
+
+class mwi_solve_info(C.Structure):
+    _fields_ = [("iters_max", C.c_int32), ("inner_total", C.c_int32), ("n_converged", C.c_int32),
+                ("n_perturbed", C.c_int32), ("resid_max", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "mwi_mesh_create": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.POINTER(_vp)],
+    "mwi_mesh_ndof": [_vp, _i64p],
+    "mwi_mesh_dof_keys": [_vp, _i32p, _i64p],
+    "mwi_mesh_destroy": [_vp],
+    "mwi_assemble": [_vp, _dp, C.c_double, C.POINTER(mwi_solver_opts), _vp, C.POINTER(_vp)],
+    "mwi_assemble_device": [_vp, _vp, C.c_double, C.POINTER(mwi_solver_opts), _vp, C.POINTER(_vp)],
+    "mwi_update_eps": [_vp, _dp],
+    "mwi_update_eps_device": [_vp, _vp],
+    "mwi_forward_solve": [_vp, C.POINTER(mwi_antenna), C.c_int32, C.POINTER(mwi_antenna), C.c_int32, _dp,
+                          C.POINTER(mwi_solve_info)],
+    "mwi_misfit_and_gradient": [_vp, _dp, _dp, _dp, _dp, C.POINTER(mwi_solve_info)],
+    "mwi_misfit_and_gradient_device": [_vp, _vp, _vp, _dp, _vp, C.POINTER(mwi_solve_info)],
+    "mwi_fields_device": [_vp, C.c_int32, C.POINTER(_vp), _i64p, _i64p],
+    "mwi_copy_fields": [_vp, C.c_int32, _dp],
+    "mwi_problem_destroy": [_vp],
+    "mwi_spmm_device": [_vp, _vp, _vp, C.c_int32],
+    "mwi_oras_apply_device": [_vp, _vp, _vp, C.c_int32],
+    "mwi_matrix_csr": [_vp, _i64p, _i64p, _i32p, _dp],
+    "mwi_decomposition": [_vp, _i32p, _i64p],
+    "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
+    "mwi_kernel_times": [_vp, _dp, _i64p],
+}
+EXPORTED = sorted(list(_SIGS) + ["mwi_last_error"])
+
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+    globals()[_name] = _f
+_lib.mwi_last_error.argtypes = []
+_lib.mwi_last_error.restype = C.c_char_p
+mwi_last_error = _lib.mwi_last_error
+
+
+def check(status, allow=()):
+    if status != MWI_OK and status not in allow:
+        raise MwiError(status, (mwi_last_error() or b"").decode())
+    return status
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _antennas(arr):
+    arr = np.asarray(arr, dtype=np.float64).reshape(-1, 8)
+    out = (mwi_antenna * arr.shape[0])()
+    for i, row in enumerate(arr):
+        out[i].pos[:] = row[0:3]
+        out[i].dir[:] = row[3:6]
+        out[i].re_I = row[6]
+        out[i].im_I = row[7]
+    return out
+
+
+def make_opts(**kw):
+    o = mwi_solver_opts()
+    part = kw.pop("part", None)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    keep = None
+    if part is not None:
+        keep = np.ascontiguousarray(part, dtype=np.int32)
+        o.part = _ptr(keep, C.c_int32)
+    return o, keep
+
+
+class Mesh:
+    """Owns an mwi_mesh_t."""
+
+    def __init__(self, xyz, tet, bface_tag, order=1):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.tet = np.ascontiguousarray(tet, dtype=np.int32)
+        tag = np.ascontiguousarray(bface_tag, dtype=np.int32)
+        self.nt = self.tet.shape[0]
+        self.order = order
+        h = _vp()
+        check(mwi_mesh_create(_ptr(self.xyz, C.c_double), self.xyz.shape[0], _ptr(self.tet, C.c_int32), self.nt,
+                              _ptr(tag, C.c_int32), order, C.byref(h)))
+        self.h = h
+        n = C.c_int64()
+        check(mwi_mesh_ndof(h, C.byref(n)))
+        self.ndof = n.value
+
+    def dof_keys(self):
+        kind = np.empty(self.ndof, dtype=np.int32)
+        verts = np.empty((self.ndof, 3), dtype=np.int64)
+        check(mwi_mesh_dof_keys(self.h, _ptr(kind, C.c_int32), _ptr(verts, C.c_int64)))
+        return kind, verts
+
+    def close(self):
+        if self.h:
+            check(mwi_mesh_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            if self.h:
+                mwi_mesh_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Problem:
+    """Owns an mwi_problem_t (assembled operator, ORAS factors, resident fields)."""
+
+    def __init__(self, mesh, eps, freq, stream=None, **opts):
+        import torch
+
+        self.mesh = mesh
+        self.freq = freq
+        self.opts, self._part = make_opts(**opts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _vp()
+        if isinstance(eps, torch.Tensor):
+            e = eps.to(torch.complex128).contiguous()
+            check(mwi_assemble_device(mesh.h, _vp(e.data_ptr()), freq, C.byref(self.opts),
+                                      _vp(stream.cuda_stream), C.byref(h)))
+        else:
+            e = np.ascontiguousarray(eps, dtype=np.complex128)
+            check(mwi_assemble(mesh.h, _ptr(e.view(np.float64), C.c_double), freq, C.byref(self.opts),
+                               _vp(stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.info = mwi_solve_info()
+
+    def update_eps(self, eps):
+        import torch
+        if isinstance(eps, torch.Tensor):
+            e = eps.to(torch.complex128).contiguous()
+            check(mwi_update_eps_device(self.h, _vp(e.data_ptr())))
+        else:
+            e = np.ascontiguousarray(eps, dtype=np.complex128)
+            check(mwi_update_eps(self.h, _ptr(e.view(np.float64), C.c_double)))
+
+    def forward_solve(self, tx, rx, allow_notconv=False):
+        t = _antennas(tx)
+        r = _antennas(rx)
+        S = np.empty((len(t), len(r)), dtype=np.complex128)  # column-major [n_rx, n_tx] == row-major [n_tx, n_rx]
+        info = mwi_solve_info()
+        st = mwi_forward_solve(self.h, t, len(t), r, len(r), _ptr(S.view(np.float64), C.c_double), C.byref(info))
+        check(st, allow=(MWI_ENOTCONV,) if allow_notconv else ())
+        self.info = info
+        return S.T.copy()
+
+    def misfit_and_gradient(self, S_meas, w=None, allow_notconv=False):
+        S_meas = np.asfortranarray(S_meas, dtype=np.complex128)
+        Sm = np.ascontiguousarray(S_meas.T)  # column-major storage of [n_rx, n_tx]
+        wp = None
+        if w is not None:
+            wc = np.ascontiguousarray(np.asarray(w, dtype=np.float64).T)
+            wp = _ptr(wc, C.c_double)
+        J = C.c_double()
+        grad = np.empty(self.mesh.nt, dtype=np.complex128)
+        info = mwi_solve_info()
+        st = mwi_misfit_and_gradient(self.h, _ptr(Sm.view(np.float64), C.c_double), wp, C.byref(J),
+                                     _ptr(grad.view(np.float64), C.c_double), C.byref(info))
+        check(st, allow=(MWI_ENOTCONV,) if allow_notconv else ())
+        self.info = info
+        return J.value, grad
+
+    def fields(self, which=0):
+        """Borrowed device pointer and shape (n, m) of the resident fields."""
+        p = _vp()
+        n = C.c_int64()
+        m = C.c_int64()
+        check(mwi_fields_device(self.h, which, C.byref(p), C.byref(n), C.byref(m)))
+        return p.value, n.value, m.value
+
+    def fields_host(self, which=0):
+        """Copy of the resident fields [n, m] (internal DOF order)."""
+        _, n, m = self.fields(which)
+        out = np.empty((n, m), dtype=np.complex128)
+        check(mwi_copy_fields(self.h, which, _ptr(out.view(np.float64), C.c_double)))
+        return out
+
+    def spmm(self, x):
+        import torch
+        y = torch.empty_like(x)
+        check(mwi_spmm_device(self.h, _vp(x.data_ptr()), _vp(y.data_ptr()), x.shape[1]))
+        return y
+
+    def oras_apply(self, x):
+        import torch
+        y = torch.empty_like(x)
+        check(mwi_oras_apply_device(self.h, _vp(x.data_ptr()), _vp(y.data_ptr()), x.shape[1]))
+        return y
+
+    def matrix_csr(self):
+        nnz = C.c_int64()
+        check(mwi_matrix_csr(self.h, C.byref(nnz), None, None, None))
+        rp = np.empty(self.mesh.ndof + 1, dtype=np.int64)
+        col = np.empty(nnz.value, dtype=np.int32)
+        val = np.empty(nnz.value, dtype=np.complex128)
+        check(mwi_matrix_csr(self.h, C.byref(nnz), _ptr(rp, C.c_int64), _ptr(col, C.c_int32),
+                             _ptr(val.view(np.float64), C.c_double)))
+        return rp, col, val
+
+    def decomposition(self, n_sub):
+        part = np.empty(self.mesh.nt, dtype=np.int32)
+        nloc = np.empty(n_sub, dtype=np.int64)
+        check(mwi_decomposition(self.h, _ptr(part, C.c_int32), _ptr(nloc, C.c_int64)))
+        return part, nloc
+
+    def factor_stats(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        d = C.c_double()
+        check(mwi_factor_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return dict(factor_entries=a.value, n_fronts=b.value, max_front=c.value, factor_flops=d.value)
+
+    def kernel_times(self):
+        ms = np.zeros(4)
+        cnt = np.zeros(4, dtype=np.int64)
+        check(mwi_kernel_times(self.h, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)))
+        return ms, cnt
+
+    def close(self):
+        if self.h:
+            check(mwi_problem_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            if self.h:
+                mwi_problem_destroy(self.h)
+        except Exception:
+            pass

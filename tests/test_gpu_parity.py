@@ -1,0 +1,152 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (complex128 results):
+* assembly and SpMM: the same sums in a different order, <= 1e-13 relative;
+* one ORAS application in FP64: <= 1e-10 relative (local LDL^T vs SuperLU
+  on B_i with condition numbers up to ~1e4);
+* FP64 path solved to rtol 1e-12: fields, S and gradient <= 1e-8 relative;
+* MIXED path (FP32 subdomain factors) solved to rtol 1e-9: <= 1e-6 relative.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import dd
+from tests._helpers import FREQ, chamber_case, col_rel_err, cube_case, key_perm, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_02573_gb300 import mwi
+    return mwi
+
+
+def _setup(lib, case, order=1, **opts):
+    mesh, eps, tx, rx = case
+    M = lib.Mesh(mesh.xyz, mesh.tet, mesh.bface_tag, order=order)
+    topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, order)
+    kind, verts = M.dof_keys()
+    perm = key_perm(kind, verts, topo)
+    return mesh, eps, tx, rx, M, topo, perm
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_matrix_and_spmm_parity(lib, order):
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, cube_case(4 if order == 2 else 8), order)
+    P = lib.Problem(M, eps, FREQ, n_sub=4)
+    A_o = O.assemble_system(mesh.xyz, topo, eps, FREQ).tocsr()
+    rp, col, val = P.matrix_csr()
+    import scipy.sparse as sp
+    A_l = sp.csr_matrix((val, col, rp), shape=(M.ndof, M.ndof))
+    # map library indices to oracle indices
+    Pm = sp.csr_matrix((np.ones(M.ndof), (np.arange(M.ndof), perm)), shape=(M.ndof, M.ndof))
+    A_lo = (Pm.T @ A_l @ Pm).tocsr()
+    d = abs(A_lo - A_o).max()
+    assert d <= 1e-13 * abs(A_o).max()
+    assert abs(A_l - A_l.T).max() == 0.0
+    rng = np.random.default_rng(0)
+    m = 5
+    X = rng.standard_normal((M.ndof, m)) + 1j * rng.standard_normal((M.ndof, m))
+    Xd = torch.from_numpy(X).cuda()
+    Y = P.spmm(Xd).cpu().numpy()
+    Yo = np.empty_like(Y)
+    Yo[:] = (A_o @ X[np.argsort(perm)])[perm]
+    assert rel_err(Y, Yo) <= 1e-13
+    P.close()
+
+
+def test_partition_matches_oracle_rcb(lib):
+    case = chamber_case(12, 11)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    P = lib.Problem(M, eps, FREQ, n_sub=8)
+    part, nloc = P.decomposition(8)
+    assert np.array_equal(part, dd.rcb_partition(mesh.xyz, mesh.tet, 8))
+    P.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-5)])
+def test_oras_apply_parity(lib, precision, tol):
+    case = chamber_case(12, 11)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    part = dd.rcb_partition(mesh.xyz, mesh.tet, 6)
+    P = lib.Problem(M, eps, FREQ, n_sub=6, part=part, precision=precision)
+    dec = dd.Decomposition(mesh.xyz, mesh.tet, topo, part, 1)
+    oras = dd.ORAS(dec, dd.local_matrices(mesh.xyz, topo, dec, eps, FREQ))
+    rng = np.random.default_rng(1)
+    m = 3
+    X = rng.standard_normal((M.ndof, m)) + 1j * rng.standard_normal((M.ndof, m))
+    Y = P.oras_apply(torch.from_numpy(X).cuda()).cpu().numpy()
+    inv = np.argsort(perm)
+    Yo = oras.apply(X[inv])[perm]
+    assert rel_err(Y, Yo) <= tol
+    P.close()
+
+
+@pytest.mark.parametrize("case_name", ["cube", "chamber"])
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6)])
+def test_forward_and_gradient_parity(lib, case_name, precision, rtol, tol):
+    case = cube_case(8) if case_name == "cube" else chamber_case(16, 15)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    n_sub = 4 if case_name == "cube" else 8
+    P = lib.Problem(M, eps, FREQ, n_sub=n_sub, precision=precision, rtol=rtol, max_iter=400)
+    S = P.forward_solve(tx, rx)
+    info = P.info.as_dict()
+    assert info["n_converged"] == tx.shape[0]
+    ref = O.forward(mesh.xyz, topo, eps, FREQ, tx, rx)
+    U = P.fields_host(0)
+    errs = col_rel_err(U, ref["U"][perm])
+    assert errs.max() <= tol, errs
+    assert rel_err(S, ref["S"]) <= tol
+    # misfit and gradient against seeded synthetic measurements
+    rng = np.random.default_rng(5)
+    S_meas = ref["S"] * (1 + 0.2 * rng.standard_normal(ref["S"].shape))
+    J, grad = P.misfit_and_gradient(S_meas)
+    J_o, grad_o, extra = O.misfit_and_gradient(mesh.xyz, topo, eps, FREQ, tx, rx, S_meas, fwd=ref)
+    assert abs(J - J_o) <= tol * abs(J_o)
+    assert rel_err(grad, grad_o) <= tol
+    Lam = P.fields_host(1)
+    assert col_rel_err(Lam, extra["Lam"][perm]).max() <= tol
+    P.close()
+
+
+def test_reciprocity_and_weights(lib):
+    case = chamber_case(14, 13, n_ant=6)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    P = lib.Problem(M, eps, FREQ, n_sub=8, rtol=1e-11)
+    S = P.forward_solve(tx, rx)
+    assert rel_err(S, S.T) <= 1e-9
+    w = np.random.default_rng(2).uniform(0.5, 2.0, S.shape)
+    S_meas = S * 0.9
+    J, grad = P.misfit_and_gradient(S_meas, w=w)
+    assert abs(J - 0.5 * np.sum(w * np.abs(S - S_meas) ** 2)) <= 1e-9 * J
+    P.close()
+
+
+def test_zero_misfit_gives_zero_gradient(lib):
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, cube_case(6))
+    P = lib.Problem(M, eps, FREQ, n_sub=2, rtol=1e-10)
+    S = P.forward_solve(tx, rx)
+    J, grad = P.misfit_and_gradient(S)
+    assert J == 0.0 and np.abs(grad).max() == 0.0
+    P.close()
+
+
+def test_errors_are_reported(lib):
+    mesh, eps, tx, rx = cube_case(4)
+    M = lib.Mesh(mesh.xyz, mesh.tet, mesh.bface_tag)
+    P = lib.Problem(M, eps, FREQ, n_sub=2)
+    with pytest.raises(lib.MwiError) as e:
+        P.misfit_and_gradient(np.zeros((4, 4), dtype=complex))
+    assert e.value.status == lib.MWI_ESTATE
+    with pytest.raises(lib.MwiError) as e:
+        M.close()
+    assert e.value.status == lib.MWI_ESTATE
+    P.close()
+    M.close()
