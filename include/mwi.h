@@ -163,6 +163,10 @@ mwi_status mwi_forward_solve(mwi_problem_t prob, const mwi_antenna* tx, int32_t 
 mwi_status mwi_misfit_and_gradient(mwi_problem_t prob, const double* S_meas, const double* w,
                                    double* J_out, double* dJ_deps, mwi_solve_info* info);
 
+/* Misfit only: J (Eq. defJ) for the S of the last forward solve, no adjoint
+ * solve.  S_meas, w host arrays as above. */
+mwi_status mwi_misfit(mwi_problem_t prob, const double* S_meas, const double* w, double* J_out);
+
 /* Same with device arrays: S_meas_dev, w_dev (nullable), dJ_deps_dev; J_out host. */
 mwi_status mwi_misfit_and_gradient_device(mwi_problem_t prob, const double* S_meas_dev,
                                           const double* w_dev, double* J_out,
@@ -209,10 +213,15 @@ mwi_status mwi_decomposition(mwi_problem_t prob, int32_t* part, int64_t* n_local
 mwi_status mwi_factor_stats(mwi_problem_t prob, int64_t* factor_entries, int64_t* n_fronts,
                             int64_t* max_front, double* factor_flops);
 
-/* Per-kernel timing of the last forward/adjoint solve, CUDA events on the
- * problem's stream: ms[0] SpMM, ms[1] ORAS apply, ms[2] orthogonalisation,
- * ms[3] other; counts[4] launches of each.  Enabled by opts.verbose >= 2. */
-mwi_status mwi_kernel_times(mwi_problem_t prob, double* ms, int64_t* counts);
+/* Per-kernel timing since the last reset, from CUDA events recorded on the
+ * problem's stream around every call (no synchronisation in between):
+ * ms[0] SpMM, ms[1] ORAS apply, ms[2] orthogonalisation (CGS2 + norms),
+ * ms[3] factorisation; counts[4] calls of each.  Enabled by opts.verbose >= 2.
+ * reset != 0 clears the accumulators after reading. */
+mwi_status mwi_kernel_times(mwi_problem_t prob, double* ms, int64_t* counts, int32_t reset);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t mwi_launch_count(void);
 
 #ifdef __cplusplus
 }

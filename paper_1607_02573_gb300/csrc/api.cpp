@@ -18,6 +18,7 @@ namespace mwi {
 
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+std::atomic<int64_t> g_launches{0};
 
 static const double kPi = 3.14159265358979323846;
 static const double kC0 = 299792458.0;
@@ -87,10 +88,17 @@ struct mwi_problem {
     int n_rx = 0;
     double setup_ms = 0;
     int inner_total = 0;
-    // per-kernel timing (opts.verbose >= 2)
+    // per-kernel timing (opts.verbose >= 2): event pairs recorded without
+    // synchronisation, harvested by mwi_kernel_times
     double t_ms[4] = {0, 0, 0, 0};
     int64_t t_cnt[4] = {0, 0, 0, 0};
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    struct EvPair { cudaEvent_t a, b; int slot; };
+    std::vector<EvPair> ev_used;
+    std::vector<cudaEvent_t> ev_free;
+    ~mwi_problem() {
+        for (auto& e : ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+        for (auto e : ev_free) cudaEventDestroy(e);
+    }
 };
 
 namespace {
@@ -136,18 +144,40 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     return d;
 }
 
-// timed region helper: records events around fn when enabled
+cudaEvent_t take_event(mwi_problem* P) {
+    if (!P->ev_free.empty()) {
+        cudaEvent_t e = P->ev_free.back();
+        P->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    MWI_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+// timed region helper: records an event pair around fn when enabled
 template <typename Fn>
 void timed(mwi_problem* P, int slot, Fn&& fn) {
     if (P->opts.verbose < 2) { fn(); return; }
-    MWI_CUDA(cudaEventRecord(P->ev0, P->st));
+    cudaEvent_t a = take_event(P), b = take_event(P);
+    MWI_CUDA(cudaEventRecord(a, P->st));
     fn();
-    MWI_CUDA(cudaEventRecord(P->ev1, P->st));
-    MWI_CUDA(cudaEventSynchronize(P->ev1));
-    float ms = 0;
-    MWI_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
-    P->t_ms[slot] += ms;
-    P->t_cnt[slot] += 1;
+    MWI_CUDA(cudaEventRecord(b, P->st));
+    P->ev_used.push_back({a, b, slot});
+}
+
+void harvest_events(mwi_problem* P) {
+    if (P->ev_used.empty()) return;
+    MWI_CUDA(cudaStreamSynchronize(P->st));
+    for (auto& e : P->ev_used) {
+        float ms = 0;
+        MWI_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
+        P->t_ms[e.slot] += ms;
+        P->t_cnt[e.slot] += 1;
+        P->ev_free.push_back(e.a);
+        P->ev_free.push_back(e.b);
+    }
+    P->ev_used.clear();
 }
 
 void build_mesh_device(mwi_mesh* M) {
@@ -284,10 +314,10 @@ void numeric_setup(mwi_problem* P) {
     MWI_CUDA(cudaMemsetAsync(P->perturbed.p, 0, sizeof(int), st));
     if (mixed) {
         P->ws32.ensure(E.F.ws_entries);
-        factorize_fronts<float2>(E.F, P->Bval.p, P->ws32.p, P->perturbed.p, st);
+        timed(P, 3, [&] { factorize_fronts<float2>(E.F, P->Bval.p, P->ws32.p, P->perturbed.p, st); });
     } else {
         P->ws64.ensure(E.F.ws_entries);
-        factorize_fronts<double2>(E.F, P->Bval.p, P->ws64.p, P->perturbed.p, st);
+        timed(P, 3, [&] { factorize_fronts<double2>(E.F, P->Bval.p, P->ws64.p, P->perturbed.p, st); });
     }
     MWI_CUDA(cudaMemcpyAsync(&P->n_perturbed, P->perturbed.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     MWI_CUDA(cudaStreamSynchronize(st));
@@ -308,8 +338,6 @@ void create_problem(mwi_mesh* M, const double* eps, bool eps_dev, double freq, c
     P->st = (cudaStream_t)stream;
     P->freq = freq;
     P->k0 = 2.0 * kPi * freq / kC0;
-    MWI_CUDA(cudaEventCreate(&P->ev0));
-    MWI_CUDA(cudaEventCreate(&P->ev1));
     {
         std::lock_guard<std::mutex> lk(M->mu);
         ensure_global(M);
@@ -429,6 +457,9 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
         convert_c64_to_c128(nm, P->x32.p, y, st);
     };
 
+    auto tfn = [P](int slot, const std::function<void()>& fn) { timed(P, slot, fn); };
+    P->outer.timer = tfn;
+    P->inner.timer = tfn;
     const double t0 = now_ms();
     P->inner_total = 0;
     P->outer.column_norms2(B, b2, st);
@@ -568,7 +599,6 @@ mwi_status mwi_forward_solve(mwi_problem_t P, const mwi_antenna* tx, int32_t n_t
         P->U.ensure(nm);
         MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));
         launch_rhs(m, P->tx_dof_d.p, P->tx_sign_d.p, P->cur_d.p, 2.0 * kPi * P->freq * kMu0, P->Brhs.p, st);
-        for (int k = 0; k < 4; ++k) { P->t_ms[k] = 0; P->t_cnt[k] = 0; }
         P->m_fwd = m;
         P->n_rx = n_rx;
         try {
@@ -639,6 +669,28 @@ static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const 
     return g != MWI_OK ? g : status;
 }
 
+mwi_status mwi_misfit(mwi_problem_t P, const double* S_meas, const double* w, double* J_out) {
+    return guard([&] {
+        MWI_REQUIRE(P && S_meas && J_out, MWI_EINVAL, "null argument");
+        MWI_REQUIRE(P->have_fwd, MWI_ESTATE, "misfit needs a prior forward_solve");
+        cudaStream_t st = P->st;
+        const int cnt = P->n_rx * P->m_fwd;
+        P->Smeas_d.ensure(cnt);
+        P->r_d.ensure(cnt);
+        P->J_d.ensure(1);
+        MWI_CUDA(cudaMemcpyAsync(P->Smeas_d.p, S_meas, cnt * sizeof(double2), cudaMemcpyHostToDevice, st));
+        const double* wd = nullptr;
+        if (w) {
+            P->w_d.ensure(cnt);
+            MWI_CUDA(cudaMemcpyAsync(P->w_d.p, w, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+            wd = P->w_d.p;
+        }
+        launch_misfit(cnt, P->S_d.p, P->Smeas_d.p, wd, P->r_d.p, P->J_d.p, st);
+        MWI_CUDA(cudaMemcpyAsync(J_out, P->J_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
 mwi_status mwi_misfit_and_gradient(mwi_problem_t prob, const double* S_meas, const double* w, double* J_out,
                                    double* dJ_deps, mwi_solve_info* info) {
     return misfit_grad_impl(prob, S_meas, w, J_out, dJ_deps, info, false);
@@ -676,8 +728,6 @@ mwi_status mwi_problem_destroy(mwi_problem_t P) {
     return guard([&] {
         if (!P) return;
         if (P->st) cudaStreamSynchronize(P->st);
-        if (P->ev0) cudaEventDestroy(P->ev0);
-        if (P->ev1) cudaEventDestroy(P->ev1);
         P->mesh->refcount--;
         delete P;
     });
@@ -752,14 +802,18 @@ mwi_status mwi_factor_stats(mwi_problem_t P, int64_t* factor_entries, int64_t* n
     });
 }
 
-mwi_status mwi_kernel_times(mwi_problem_t P, double* ms, int64_t* counts) {
+mwi_status mwi_kernel_times(mwi_problem_t P, double* ms, int64_t* counts, int32_t reset) {
     return guard([&] {
         MWI_REQUIRE(P, MWI_EINVAL, "null problem");
+        harvest_events(P);
         for (int k = 0; k < 4; ++k) {
             if (ms) ms[k] = P->t_ms[k];
             if (counts) counts[k] = P->t_cnt[k];
+            if (reset) { P->t_ms[k] = 0; P->t_cnt[k] = 0; }
         }
     });
 }
+
+int64_t mwi_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"

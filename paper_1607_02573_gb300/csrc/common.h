@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
 #include <stdexcept>
 #include <string>
@@ -22,6 +23,9 @@ struct Error : public std::runtime_error {
 
 void set_last_error(const std::string& msg);
 
+// kernels launched by this library (every launch site ends in MWI_CHECK_LAUNCH)
+extern std::atomic<int64_t> g_launches;
+
 #define MWI_CUDA(call)                                                                  \
     do {                                                                                \
         cudaError_t err__ = (call);                                                     \
@@ -31,7 +35,11 @@ void set_last_error(const std::string& msg);
                                               __FILE__ + ":" + std::to_string(__LINE__)); \
     } while (0)
 
-#define MWI_CHECK_LAUNCH() MWI_CUDA(cudaGetLastError())
+#define MWI_CHECK_LAUNCH()                                           \
+    do {                                                             \
+        ::mwi::g_launches.fetch_add(1, std::memory_order_relaxed);   \
+        MWI_CUDA(cudaGetLastError());                                \
+    } while (0)
 
 #define MWI_REQUIRE(cond, status, msg)                     \
     do {                                                   \

@@ -22,6 +22,8 @@ struct Gmres {
     DevBuf<double2> H, cs, sn, g, y, h, hacc, partial;
     DevBuf<double> dvec;
     DevBuf<int> ivec;
+    // optional timer: runs fn, attributing its device time to a slot
+    std::function<void(int, const std::function<void()>&)> timer;
 
     void reserve(int64_t n, int m, int restart);
     // One flexible GMRES cycle from residual r0 (initial x in x, updated in

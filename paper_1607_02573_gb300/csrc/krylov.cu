@@ -333,13 +333,17 @@ int Gmres<C>::cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const doubl
         M(vk, zk);
         A(zk, W.p);
         // CGS2
-        MWI_CUDA(cudaMemsetAsync(hacc.p, 0, (size_t)(k + 1) * m * sizeof(double2), st));
-        for (int pass = 0; pass < 2; ++pass) {
-            dots(V.p, k + 1, vs, W.p, h.p, hacc.p, st);
-            cgs_update_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, k + 1, V.p, vs, h.p, W.p);
-            MWI_CHECK_LAUNCH();
-        }
-        column_norms2(W.p, hn2, st);
+        auto ortho = [&] {
+            MWI_CUDA(cudaMemsetAsync(hacc.p, 0, (size_t)(k + 1) * m * sizeof(double2), st));
+            for (int pass = 0; pass < 2; ++pass) {
+                dots(V.p, k + 1, vs, W.p, h.p, hacc.p, st);
+                cgs_update_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, k + 1, V.p, vs, h.p, W.p);
+                MWI_CHECK_LAUNCH();
+            }
+            column_norms2(W.p, hn2, st);
+        };
+        if (timer) timer(2, ortho);
+        else ortho();
         MWI_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), st));
         arnoldi_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, k, restart, hacc.p, hn2, H.p, cs.p, sn.p, g.p, active,
                                                         kcol, tol, resid, inv, nact);

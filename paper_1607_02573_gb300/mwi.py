@@ -75,9 +75,10 @@ _SIGS = {
     "mwi_matrix_csr": [_vp, _i64p, _i64p, _i32p, _dp],
     "mwi_decomposition": [_vp, _i32p, _i64p],
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
-    "mwi_kernel_times": [_vp, _dp, _i64p],
+    "mwi_kernel_times": [_vp, _dp, _i64p, C.c_int32],
+    "mwi_misfit": [_vp, _dp, _dp, _dp],
 }
-EXPORTED = sorted(list(_SIGS) + ["mwi_last_error"])
+EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count"])
 
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -87,6 +88,9 @@ for _name, _args in _SIGS.items():
 _lib.mwi_last_error.argtypes = []
 _lib.mwi_last_error.restype = C.c_char_p
 mwi_last_error = _lib.mwi_last_error
+_lib.mwi_launch_count.argtypes = []
+_lib.mwi_launch_count.restype = C.c_int64
+mwi_launch_count = _lib.mwi_launch_count
 
 
 def check(status, allow=()):
@@ -266,11 +270,21 @@ class Problem:
         check(mwi_factor_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         return dict(factor_entries=a.value, n_fronts=b.value, max_front=c.value, factor_flops=d.value)
 
-    def kernel_times(self):
+    def kernel_times(self, reset=True):
         ms = np.zeros(4)
         cnt = np.zeros(4, dtype=np.int64)
-        check(mwi_kernel_times(self.h, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)))
+        check(mwi_kernel_times(self.h, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64), 1 if reset else 0))
         return ms, cnt
+
+    def misfit(self, S_meas, w=None):
+        Sm = np.ascontiguousarray(np.asarray(S_meas, dtype=np.complex128).T)
+        wp = None
+        if w is not None:
+            wc = np.ascontiguousarray(np.asarray(w, dtype=np.float64).T)
+            wp = _ptr(wc, C.c_double)
+        J = C.c_double()
+        check(mwi_misfit(self.h, _ptr(Sm.view(np.float64), C.c_double), wp, C.byref(J)))
+        return J.value
 
     def close(self):
         if self.h:
