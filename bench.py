@@ -135,9 +135,10 @@ def run_mine(args, rank, world):
         P = mwi.Problem(M, eps_d, FREQ, stream=stream, n_sub=64, precision=precision, rtol=RTOL,
                         verbose=2, max_iter=500)
         fs = P.factor_stats()
-        # synthetic measurements: S of the target map plus 1 % noise, from this same solver
+        # synthetic measurements: S of the two-inclusion target map plus 1 % noise
+        from synthetic import add_noise, chamber_target_eps
+        P.update_eps(torch.from_numpy(chamber_target_eps(mesh.xyz, mesh.tet)).to(dev))
         S_t = P.forward_solve(ants, ants)
-        from synthetic import add_noise
         S_meas = add_noise(S_t, eta=0.01, seed=1234)
         S_meas_d = torch.from_numpy(np.ascontiguousarray(S_meas.T)).to(dev)  # column-major [n_rx, n_tx]
         grad_d = torch.empty(mesh.nt, dtype=torch.complex128, device=dev)
