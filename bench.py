@@ -232,11 +232,11 @@ def roofline(res, ndof, m):
 
 def cpu_baseline(args, steps=1):
     """The oracle as it stands (SciPy SuperLU direct solve, complex128) on a
-    bounded sample: the same chamber geometry, materials and ring at a
-    coarser grid (16 x 16 x 15 hexes, 21.6k tets), 32 Tx + 32 adjoint columns."""
+    bounded sample: the same chamber geometry, materials and a 32-antenna ring
+    at a coarser grid (12 x 12 x 11 hexes), 32 Tx + 32 adjoint columns."""
     import oracle as O
     from synthetic import add_noise, antenna_array, chamber_eps, chamber_mesh, ring_antennas
-    mesh = chamber_mesh(16, 15)
+    mesh = chamber_mesh(12, 11)
     eps = chamber_eps(mesh.xyz, mesh.tet)
     ants = antenna_array(ring_antennas(32, radius=0.1))
     topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, 1)
@@ -248,7 +248,7 @@ def cpu_baseline(args, steps=1):
     dt = (time.perf_counter() - t0) / steps
     cores = len(os.sched_getaffinity(0))
     return {"value": 64 / dt, "unit": UNIT, "cores": 1, "host_cores": cores, "kind": "oracle",
-            "sample": f"oracle direct LU (SuperLU, 1 thread) forward+adjoint+gradient on the 16x16x15 chamber "
+            "sample": f"oracle direct LU (SuperLU, 1 thread) forward+adjoint+gradient on the 12x12x11 chamber "
                       f"({mesh.nt} tets, {topo.ndof} DOF), 32+32 columns; {dt:.1f} s per step"}
 
 

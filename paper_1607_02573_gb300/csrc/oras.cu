@@ -51,25 +51,33 @@ __global__ void scatter_kernel(int64_t n, int m, const int64_t* __restrict__ own
     y[e] = cvt<C, Out>(acc);
 }
 
-template <typename C>
+// Forward sweep of one front for columns [c0, c0 + rc): w holds the front's
+// rows (pivots from Y, update rows zero, plus the children's update vectors);
+// per block of 32 pivot columns: the unit-lower diagonal triangle is solved by
+// one warp per column with shuffles, then every row below the block subtracts
+// its block of L times the solved block (one thread per row, all RC columns in
+// registers, each L entry read once, coalesced along the column).
+template <typename C, int RC>
 __global__ void __launch_bounds__(256) forward_kernel(
     const int32_t* __restrict__ level_fronts, int lo, const int32_t* __restrict__ P, const int32_t* __restrict__ U,
     const int32_t* __restrict__ start, const int32_t* __restrict__ sub, const int64_t* __restrict__ sub_off,
     const int64_t* __restrict__ f_off, const int64_t* __restrict__ u_off, const int64_t* __restrict__ upd_row,
     const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child, const int32_t* __restrict__ urel,
-    const C* __restrict__ ws, C* __restrict__ Y, C* __restrict__ upd, int m, int RC) {
+    const C* __restrict__ ws, C* __restrict__ Y, C* __restrict__ upd, int m) {
+    constexpr int RP = RC + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* w = reinterpret_cast<C*>(smem_raw);
+    __shared__ C Ld[32][33];
     const int s = level_fronts[lo + blockIdx.y];
     const int c0 = blockIdx.x * RC;
     const int rc = min(RC, m - c0);
     const int p = P[s], u = U[s];
     const int f = p + u;
     const int64_t rowbase = sub_off[sub[s]] + start[s];
-    const int tid = threadIdx.x, nth = blockDim.x;
-    for (int e = tid; e < f * RC; e += nth) {
-        int i = e / RC, r = e - i * RC;
-        w[e] = (i < p && r < rc) ? Y[(rowbase + i) * m + c0 + r] : czero<C>();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < f * RC; e += 256) {
+        const int i = e / RC, r = e - i * RC;
+        w[i * RP + r] = (i < p && r < rc) ? Y[(rowbase + i) * m + c0 + r] : czero<C>();
     }
     __syncthreads();
     for (int q = child_ptr[s]; q < child_ptr[s + 1]; ++q) {
@@ -77,11 +85,11 @@ __global__ void __launch_bounds__(256) forward_kernel(
         const int uc = U[c];
         const int32_t* rel = urel + u_off[c];
         const C* src = upd + upd_row[c] * m + c0;
-        for (int e = tid; e < uc * RC; e += nth) {
-            int k = e / RC, r = e - k * RC;
+        for (int e = tid; e < uc * RC; e += 256) {
+            const int k = e / RC, r = e - k * RC;
             if (r < rc) {
-                C v = src[(int64_t)k * m + r];
-                C& d = w[rel[k] * RC + r];
+                const C v = src[(int64_t)k * m + r];
+                C& d = w[rel[k] * RP + r];
                 d.x += v.x;
                 d.y += v.y;
             }
@@ -90,40 +98,62 @@ __global__ void __launch_bounds__(256) forward_kernel(
     }
     const C* L = ws + f_off[s];
     for (int jb = 0; jb < p; jb += 32) {
-        const int je = min(jb + 32, p);
-        for (int j = jb; j < je - 1; ++j) {
-            const int nr = je - j - 1;
-            for (int e = tid; e < nr * RC; e += nth) {
-                int i = j + 1 + e / RC, r = e % RC;
-                w[i * RC + r] = cfms(L[(int64_t)j * f + i], w[j * RC + r], w[i * RC + r]);
-            }
-            __syncthreads();
+        const int nb = min(32, p - jb);
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int i = e & 31, j = e >> 5;
+            Ld[i][j] = (i < nb && j < i) ? L[(int64_t)(jb + j) * f + jb + i] : czero<C>();
         }
-        const int nr = f - je;
-        for (int e = tid; e < nr * RC; e += nth) {
-            int i = je + e / RC, r = e % RC;
-            C acc = w[i * RC + r];
-            for (int j = jb; j < je; ++j) acc = cfms(L[(int64_t)j * f + i], w[j * RC + r], acc);
-            w[i * RC + r] = acc;
+        __syncthreads();
+        if (warp < RC) {
+            C val = lane < nb ? w[(jb + lane) * RP + warp] : czero<C>();
+            for (int j = 0; j < nb; ++j) {
+                C x;
+                x.x = __shfl_sync(0xffffffffu, val.x, j);
+                x.y = __shfl_sync(0xffffffffu, val.y, j);
+                val = cfms(Ld[lane][j], x, val);
+            }
+            if (lane < nb) w[(jb + lane) * RP + warp] = val;
+        }
+        __syncthreads();
+        for (int i = jb + nb + tid; i < f; i += 256) {
+            C acc[RC];
+#pragma unroll
+            for (int r = 0; r < RC; ++r) acc[r] = w[i * RP + r];
+            const C* Lc = L + (int64_t)jb * f + i;
+#pragma unroll 4
+            for (int j = 0; j < nb; ++j) {
+                const C l = Lc[(int64_t)j * f];
+                const C* wj = w + (jb + j) * RP;
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[r] = cfms(l, wj[r], acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RC; ++r) w[i * RP + r] = acc[r];
         }
         __syncthreads();
     }
-    for (int e = tid; e < f * RC; e += nth) {
-        int i = e / RC, r = e - i * RC;
+    for (int e = tid; e < f * RC; e += 256) {
+        const int i = e / RC, r = e - i * RC;
         if (r >= rc) continue;
-        if (i < p) Y[(rowbase + i) * m + c0 + r] = cmul(w[e], crecip(L[(int64_t)i * f + i]));
-        else upd[(upd_row[s] + i - p) * m + c0 + r] = w[e];
+        if (i < p) Y[(rowbase + i) * m + c0 + r] = cmul(w[i * RP + r], crecip(L[(int64_t)i * f + i]));
+        else upd[(upd_row[s] + i - p) * m + c0 + r] = w[i * RP + r];
     }
 }
 
-template <typename C>
+// Backward sweep: per block of 32 pivots (last block first), subtract the
+// dots of the block's L columns with the already final rows below (warp per
+// 4 columns, lanes along the rows, shuffle reduction), then solve the
+// transposed unit-lower triangle with one warp per column.
+template <typename C, int RC>
 __global__ void __launch_bounds__(256) backward_kernel(
     const int32_t* __restrict__ level_fronts, int lo, const int32_t* __restrict__ P, const int32_t* __restrict__ U,
     const int32_t* __restrict__ start, const int32_t* __restrict__ sub, const int64_t* __restrict__ sub_off,
     const int64_t* __restrict__ f_off, const int64_t* __restrict__ u_off, const int32_t* __restrict__ urows,
-    const C* __restrict__ ws, C* __restrict__ Y, int m, int RC) {
+    const C* __restrict__ ws, C* __restrict__ Y, int m) {
+    constexpr int RP = RC + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* w = reinterpret_cast<C*>(smem_raw);
+    __shared__ C Ld[32][33];
     const int s = level_fronts[lo + blockIdx.y];
     const int c0 = blockIdx.x * RC;
     const int rc = min(RC, m - c0);
@@ -132,108 +162,142 @@ __global__ void __launch_bounds__(256) backward_kernel(
     const int64_t sbase = sub_off[sub[s]];
     const int64_t rowbase = sbase + start[s];
     const int32_t* ur = urows + u_off[s];
-    const int tid = threadIdx.x, nth = blockDim.x;
-    for (int e = tid; e < f * RC; e += nth) {
-        int i = e / RC, r = e - i * RC;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < f * RC; e += 256) {
+        const int i = e / RC, r = e - i * RC;
         C v = czero<C>();
         if (r < rc) v = i < p ? Y[(rowbase + i) * m + c0 + r] : Y[(sbase + ur[i - p]) * m + c0 + r];
-        w[e] = v;
+        w[i * RP + r] = v;
     }
-    __syncthreads();
     const C* L = ws + f_off[s];
-    const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const int nblk = (p + 31) / 32;
     for (int bk = nblk - 1; bk >= 0; --bk) {
-        const int jb = bk * 32, je = min(jb + 32, p);
-        // w[j] -= sum_{i >= je} L[i][j] w[i]   (warp per j, lanes over i)
-        for (int j = jb + warp; j < je; j += nwarp) {
-            C acc[8];
+        const int jb = bk * 32, nb = min(32, p - jb), je = jb + nb;
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int i = e & 31, j = e >> 5;
+            Ld[i][j] = (i < nb && j < i) ? L[(int64_t)(jb + j) * f + jb + i] : czero<C>();
+        }
+        __syncthreads();
+        {
+            C acc[4][RC];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) acc[r] = czero<C>();
-            const C* Lc = L + (int64_t)j * f;
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[q][r] = czero<C>();
             for (int i = je + lane; i < f; i += 32) {
-                C l = Lc[i];
+                C x[RC];
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
-                    if (r < RC) acc[r] = cfma(l, w[i * RC + r], acc[r]);
+                for (int r = 0; r < RC; ++r) x[r] = w[i * RP + r];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int jj = warp + 8 * q;
+                    if (jj < nb) {
+                        const C l = L[(int64_t)(jb + jj) * f + i];
+#pragma unroll
+                        for (int r = 0; r < RC; ++r) acc[q][r] = cfma(l, x[r], acc[q][r]);
+                    }
+                }
             }
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                if (r >= RC) break;
-                C a = acc[r];
-                for (int o = 16; o > 0; o >>= 1) {
-                    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
-                    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int r = 0; r < RC; ++r)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        acc[q][r].x += __shfl_xor_sync(0xffffffffu, acc[q][r].x, o);
+                        acc[q][r].y += __shfl_xor_sync(0xffffffffu, acc[q][r].y, o);
+                    }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int jj = warp + 8 * q;
+                if (jj < nb) {
+#pragma unroll
+                    for (int r = 0; r < RC; ++r)
+                        if (lane == r) w[(jb + jj) * RP + r] = csub(w[(jb + jj) * RP + r], acc[q][r]);
                 }
-                if (lane == 0) w[j * RC + r] = csub(w[j * RC + r], a);
             }
         }
         __syncthreads();
-        for (int j = je - 1; j > jb; --j) {
-            const int nr = j - jb;
-            for (int e = tid; e < nr * RC; e += nth) {
-                int i = jb + e / RC, r = e % RC;
-                w[i * RC + r] = cfms(L[(int64_t)i * f + j], w[j * RC + r], w[i * RC + r]);
+        if (warp < RC) {
+            C val = lane < nb ? w[(jb + lane) * RP + warp] : czero<C>();
+            for (int j = nb - 1; j > 0; --j) {
+                C x;
+                x.x = __shfl_sync(0xffffffffu, val.x, j);
+                x.y = __shfl_sync(0xffffffffu, val.y, j);
+                if (lane < j) val = cfms(Ld[j][lane], x, val);
             }
-            __syncthreads();
+            if (lane < nb) w[(jb + lane) * RP + warp] = val;
         }
+        __syncthreads();
     }
-    for (int e = tid; e < p * RC; e += nth) {
-        int i = e / RC, r = e - i * RC;
-        if (r < rc) Y[(rowbase + i) * m + c0 + r] = w[e];
+    for (int e = tid; e < p * RC; e += 256) {
+        const int i = e / RC, r = e - i * RC;
+        if (r < rc) Y[(rowbase + i) * m + c0 + r] = w[i * RP + r];
     }
 }
 
-static int choose_rc(int m, int fmax, size_t elt) {
-    int rc = 8;
-    while (rc > 1 && (rc > m || (size_t)fmax * rc * elt > 160 * 1024)) rc >>= 1;
+template <typename C> struct SweepCfg;
+template <> struct SweepCfg<float2> { static constexpr int RCMAX = 8; };
+template <> struct SweepCfg<double2> { static constexpr int RCMAX = 4; };
+
+static int choose_rc(int m, int fmax, size_t elt, int rcmax) {
+    int rc = rcmax;
+    while (rc > 1 && (rc > m || (size_t)fmax * (rc + 1) * elt > 180 * 1024)) rc >>= 1;
     return rc;
 }
 
-template <typename C>
-static void set_smem_attr() {
+static const size_t kSweepSmem = 200 * 1024;
+
+template <typename C, int RC>
+static void set_attr_rc() {
     static bool done = false;
     if (!done) {
-        MWI_CUDA(cudaFuncSetAttribute(forward_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        MWI_CUDA(cudaFuncSetAttribute(backward_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        MWI_CUDA(cudaFuncSetAttribute(forward_kernel<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
+        MWI_CUDA(cudaFuncSetAttribute(backward_kernel<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSweepSmem));
         done = true;
+    }
+}
+
+template <typename C, int RC>
+static void sweep_level(const FrontsDev& F, const C* ws, C* Y, C* upd, int m, int l, bool fwd, cudaStream_t st) {
+    set_attr_rc<C, RC>();
+    const size_t sm = (size_t)F.level_fmax[l] * (RC + 1) * sizeof(C);
+    MWI_REQUIRE(sm <= kSweepSmem, MWI_EINVAL, "front too large for the shared-memory solve");
+    for (int lo = F.level_ptr[l]; lo < F.level_ptr[l + 1]; lo += 65535) {
+        const int nf = std::min(65535, F.level_ptr[l + 1] - lo);
+        dim3 grd((m + RC - 1) / RC, nf);
+        if (fwd)
+            forward_kernel<C, RC><<<grd, 256, sm, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.start.p, F.sub.p,
+                                                        F.sub_off.p, F.f_off.p, F.u_off.p, F.upd_row.p,
+                                                        F.child_ptr.p, F.child.p, F.urel.p, ws, Y, upd, m);
+        else
+            backward_kernel<C, RC><<<grd, 256, sm, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.start.p, F.sub.p,
+                                                         F.sub_off.p, F.f_off.p, F.u_off.p, F.urows.p, ws, Y, m);
+        MWI_CHECK_LAUNCH();
+    }
+}
+
+template <typename C>
+static void sweep(const FrontsDev& F, const C* ws, C* Y, C* upd, int m, int l, bool fwd, cudaStream_t st) {
+    const int rc = choose_rc(m, F.level_fmax[l], sizeof(C), SweepCfg<C>::RCMAX);
+    switch (rc) {
+        case 8: sweep_level<C, 8>(F, ws, Y, upd, m, l, fwd, st); break;
+        case 4: sweep_level<C, 4>(F, ws, Y, upd, m, l, fwd, st); break;
+        case 2: sweep_level<C, 2>(F, ws, Y, upd, m, l, fwd, st); break;
+        default: sweep_level<C, 1>(F, ws, Y, upd, m, l, fwd, st); break;
     }
 }
 
 template <typename C, typename In, typename Out>
 static void oras_apply_impl(const FrontsDev& F, const C* ws, const In* x, Out* y, int m, C* Y, C* upd,
                             cudaStream_t st) {
-    set_smem_attr<C>();
     const int th = 256;
     int64_t tot = F.nloc * m;
     gather_kernel<In, C><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(F.nloc, m, F.loc2glob.p, x, Y);
     MWI_CHECK_LAUNCH();
     const int nlev = (int)F.level_ptr.size() - 1;
-    for (int l = 0; l < nlev; ++l) {
-        const int rc = choose_rc(m, F.level_fmax[l], sizeof(C));
-        MWI_REQUIRE((size_t)F.level_fmax[l] * rc * sizeof(C) <= 200 * 1024, MWI_EINVAL,
-                    "front too large for the shared-memory solve");
-        const size_t sm = (size_t)F.level_fmax[l] * rc * sizeof(C);
-        for (int lo = F.level_ptr[l]; lo < F.level_ptr[l + 1]; lo += 65535) {
-            const int nf = std::min(65535, F.level_ptr[l + 1] - lo);
-            dim3 grd((m + rc - 1) / rc, nf);
-            forward_kernel<C><<<grd, th, sm, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.start.p, F.sub.p,
-                                                   F.sub_off.p, F.f_off.p, F.u_off.p, F.upd_row.p, F.child_ptr.p,
-                                                   F.child.p, F.urel.p, ws, Y, upd, m, rc);
-            MWI_CHECK_LAUNCH();
-        }
-    }
-    for (int l = nlev - 1; l >= 0; --l) {
-        const int rc = choose_rc(m, F.level_fmax[l], sizeof(C));
-        const size_t sm = (size_t)F.level_fmax[l] * rc * sizeof(C);
-        for (int lo = F.level_ptr[l]; lo < F.level_ptr[l + 1]; lo += 65535) {
-            const int nf = std::min(65535, F.level_ptr[l + 1] - lo);
-            dim3 grd((m + rc - 1) / rc, nf);
-            backward_kernel<C><<<grd, th, sm, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.start.p, F.sub.p,
-                                                    F.sub_off.p, F.f_off.p, F.u_off.p, F.urows.p, ws, Y, m, rc);
-            MWI_CHECK_LAUNCH();
-        }
-    }
+    for (int l = 0; l < nlev; ++l) sweep<C>(F, ws, Y, upd, m, l, true, st);
+    for (int l = nlev - 1; l >= 0; --l) sweep<C>(F, ws, Y, upd, m, l, false, st);
     // scatter into the global vector (n = own_ptr size - 1)
     const int64_t n = (int64_t)F.own_ptr.n - 1;
     tot = n * m;

@@ -150,3 +150,21 @@ def test_errors_are_reported(lib):
     assert e.value.status == lib.MWI_ESTATE
     P.close()
     M.close()
+
+
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6)])
+def test_order2_forward_and_gradient_parity(lib, precision, rtol, tol):
+    case = cube_case(4)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case, order=2)
+    P = lib.Problem(M, eps, FREQ, n_sub=3, precision=precision, rtol=rtol, max_iter=300)
+    S = P.forward_solve(tx, rx)
+    ref = O.forward(mesh.xyz, topo, eps, FREQ, tx, rx)
+    U = P.fields_host(0)
+    assert col_rel_err(U, ref["U"][perm]).max() <= tol
+    assert rel_err(S, ref["S"]) <= tol
+    S_meas = ref["S"] * 0.8
+    J, grad = P.misfit_and_gradient(S_meas)
+    J_o, grad_o, _ = O.misfit_and_gradient(mesh.xyz, topo, eps, FREQ, tx, rx, S_meas, fwd=ref)
+    assert abs(J - J_o) <= tol * abs(J_o)
+    assert rel_err(grad, grad_o) <= tol
+    P.close()
