@@ -65,13 +65,13 @@ struct mwi_problem {
     double freq = 0, k0 = 0;
     DevBuf<double2> eps, A_coef, B_coef, Aval, Bval;
     DevBuf<float2> Aval32;
-    DevBuf<double2> ws64;
-    DevBuf<float2> ws32;
+    DevBuf<double2> ws64, inv64, sch64[2];
+    DevBuf<float2> ws32, inv32, sch32[2];
     DevBuf<int> perturbed;
     int n_perturbed = 0;
     // solve state
-    DevBuf<double2> Y64, upd64;
-    DevBuf<float2> Y32, upd32;
+    DevBuf<double2> Y64, Z64, upd64;
+    DevBuf<float2> Y32, Z32, upd32;
     Gmres<double2> outer;
     Gmres<float2> inner;
     DevBuf<double2> U, Lam, Brhs, R;
@@ -253,14 +253,14 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     const size_t nf = D.fronts.size();
     F.nfronts = (int64_t)nf;
     std::vector<int32_t> start(nf), p(nf), u(nf), parent(nf), sub(nf);
-    std::vector<int64_t> f_off(nf), u_off(nf), upd_row(nf);
+    std::vector<int64_t> f_off(nf), u_off(nf), upd_row(nf), sch_off(nf);
     for (size_t k = 0; k < nf; ++k) {
         const Front& fr = D.fronts[k];
         start[k] = fr.start; p[k] = fr.p; u[k] = fr.u; parent[k] = fr.parent; sub[k] = fr.sub;
-        f_off[k] = fr.f_off; u_off[k] = fr.u_off; upd_row[k] = fr.upd_row;
+        f_off[k] = fr.f_off; u_off[k] = fr.u_off; upd_row[k] = fr.upd_row; sch_off[k] = fr.sch_off;
     }
     up(F.start, start, st); up(F.p, p, st); up(F.u, u, st); up(F.parent, parent, st); up(F.sub, sub, st);
-    up(F.f_off, f_off, st); up(F.u_off, u_off, st); up(F.upd_row, upd_row, st);
+    up(F.f_off, f_off, st); up(F.u_off, u_off, st); up(F.upd_row, upd_row, st); up(F.sch_off, sch_off, st);
     up(F.child_ptr, D.child_ptr, st); up(F.child, D.child, st);
     up(F.urows, D.urows, st); up(F.urel, D.urel, st);
     up(F.amap_front_ptr, D.amap_front_ptr, st); up(F.amap_slot, D.amap_slot, st); up(F.amap_pos, D.amap_pos, st);
@@ -285,7 +285,46 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     F.nloc = D.sub_off[D.n_sub];
     F.upd_rows = D.upd_rows;
     F.ws_entries = D.ws_entries;
+    F.level_sch = D.level_sch;
+    F.sch_entries[0] = D.sch_entries[0];
+    F.sch_entries[1] = D.sch_entries[1];
     F.n_sub = D.n_sub;
+    // GEMM tile lists of the sweeps and per-level offsets of the L11^-1 scratch
+    for (int pass = 0; pass < 2; ++pass) {
+        TileLists& TL = pass == 0 ? F.tiles64 : F.tiles32;
+        TL.tm = sweep_tile_rows(pass == 0);
+        std::vector<int2> pt, ut;
+        TL.p_ptr.assign(1, 0);
+        TL.u_ptr.assign(1, 0);
+        for (int l = 0; l < nlev; ++l) {
+            for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
+                const int sid = D.level_fronts[q];
+                const Front& fr = D.fronts[sid];
+                for (int r = 0; r < fr.p; r += TL.tm) pt.push_back(make_int2(sid, r));
+                for (int r = 0; r < fr.u; r += TL.tm) ut.push_back(make_int2(sid, r));
+            }
+            TL.p_ptr.push_back((int64_t)pt.size());
+            TL.u_ptr.push_back((int64_t)ut.size());
+        }
+        if (pt.empty()) pt.push_back(make_int2(0, 0));
+        if (ut.empty()) ut.push_back(make_int2(0, 0));
+        TL.p_tiles.upload(pt, st);
+        TL.u_tiles.upload(ut, st);
+    }
+    {
+        std::vector<int64_t> io(D.level_fronts.size());
+        F.inv_entries = 0;
+        for (int l = 0; l < nlev; ++l) {
+            int64_t acc = 0;
+            for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
+                io[q] = acc;
+                const int64_t pp = D.fronts[D.level_fronts[q]].p;
+                acc += pp * pp;
+            }
+            F.inv_entries = std::max(F.inv_entries, acc);
+        }
+        up(F.inv_off, io, st);
+    }
     MWI_CUDA(cudaStreamSynchronize(st));
     M->cache.push_back(E);
     return E;
@@ -314,10 +353,20 @@ void numeric_setup(mwi_problem* P) {
     MWI_CUDA(cudaMemsetAsync(P->perturbed.p, 0, sizeof(int), st));
     if (mixed) {
         P->ws32.ensure(E.F.ws_entries);
-        timed(P, 3, [&] { factorize_fronts<float2>(E.F, P->Bval.p, P->ws32.p, P->perturbed.p, st); });
+        P->inv32.ensure(std::max<int64_t>(1, E.F.inv_entries));
+        for (int k = 0; k < 2; ++k) P->sch32[k].ensure(std::max<int64_t>(1, E.F.sch_entries[k]));
+        float2* sch[2] = {P->sch32[0].p, P->sch32[1].p};
+        timed(P, 3, [&] {
+            factorize_fronts<float2>(E.F, P->Bval.p, P->ws32.p, sch, P->inv32.p, P->perturbed.p, st);
+        });
     } else {
         P->ws64.ensure(E.F.ws_entries);
-        timed(P, 3, [&] { factorize_fronts<double2>(E.F, P->Bval.p, P->ws64.p, P->perturbed.p, st); });
+        P->inv64.ensure(std::max<int64_t>(1, E.F.inv_entries));
+        for (int k = 0; k < 2; ++k) P->sch64[k].ensure(std::max<int64_t>(1, E.F.sch_entries[k]));
+        double2* sch[2] = {P->sch64[0].p, P->sch64[1].p};
+        timed(P, 3, [&] {
+            factorize_fronts<double2>(E.F, P->Bval.p, P->ws64.p, sch, P->inv64.p, P->perturbed.p, st);
+        });
     }
     MWI_CUDA(cudaMemcpyAsync(&P->n_perturbed, P->perturbed.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     MWI_CUDA(cudaStreamSynchronize(st));
@@ -419,12 +468,14 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     // local solve buffers
     if (mixed) {
         P->Y32.ensure((size_t)E.F.nloc * m);
+        P->Z32.ensure((size_t)E.F.nloc * m);
         P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
         P->inner.reserve(n, m, std::max(1, o.inner_iters));
         P->v32.ensure(nm);
         P->x32.ensure(nm);
     } else {
         P->Y64.ensure((size_t)E.F.nloc * m);
+        P->Z64.ensure((size_t)E.F.nloc * m);
         P->upd64.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
     }
     auto A64 = [&](const double2* x, double2* y) {
@@ -435,12 +486,14 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     };
     auto M32 = [&](const float2* x, float2* y) {
         timed(P, 1, [&] {
-            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->upd32.p, st, x, y);
+            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, x, y);
         });
     };
     auto M64 = [&](const double2* x, double2* y) {
         if (!mixed) {
-            timed(P, 1, [&] { oras_apply<double2>(E.F, P->ws64.p, x, y, m, P->Y64.p, P->upd64.p, st); });
+            timed(P, 1, [&] {
+                oras_apply<double2>(E.F, P->ws64.p, x, y, m, P->Y64.p, P->Z64.p, P->upd64.p, st);
+            });
             return;
         }
         // inner GMRES in complex FP32 on A z = x, preconditioned by the FP32 ORAS
@@ -750,17 +803,20 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
         const int64_t n = P->mesh->T.ndof;
         if (P->opts.precision == 1) {
             P->Y32.ensure((size_t)E.F.nloc * m);
+            P->Z32.ensure((size_t)E.F.nloc * m);
             P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
             P->v32.ensure(n * m);
             P->x32.ensure(n * m);
             convert_c128_to_c64(n * m, (const double2*)x_dev, P->v32.p, P->st);
-            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->upd32.p, P->st, P->v32.p, P->x32.p);
+            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, P->st, P->v32.p,
+                               P->x32.p);
             convert_c64_to_c128(n * m, P->x32.p, (double2*)y_dev, P->st);
         } else {
             P->Y64.ensure((size_t)E.F.nloc * m);
+            P->Z64.ensure((size_t)E.F.nloc * m);
             P->upd64.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
-            oras_apply<double2>(E.F, P->ws64.p, (const double2*)x_dev, (double2*)y_dev, m, P->Y64.p, P->upd64.p,
-                                P->st);
+            oras_apply<double2>(E.F, P->ws64.p, (const double2*)x_dev, (double2*)y_dev, m, P->Y64.p, P->Z64.p,
+                                P->upd64.p, P->st);
         }
         MWI_CUDA(cudaStreamSynchronize(P->st));
     });

@@ -11,9 +11,15 @@
 // depth first: assemble (entries of B_i, then extend-add of the children's
 // Schur complements), then a blocked right-looking partial factorisation of
 // the p pivot columns (panel kernel + trailing-update kernel) that leaves the
-// Schur complement in the front's trailing block for the parent.
-// Fronts are dense, column-major f x f, lower triangle used; the first p
-// columns hold L (unit diagonal implied) with D on the diagonal.
+// Schur complement for the parent.
+// A front (dense, f = p + u, lower triangle used) is stored in two pieces:
+// its p pivot columns as a column-major f x p panel in the factor store (L
+// with unit diagonal implied, D on the diagonal), and its u x u Schur block in
+// a transient buffer shared by the fronts of one level (two buffers, even and
+// odd levels, since a level's blocks are consumed by the next level).  Once a
+// level is factorised, the p x p unit-lower block L11 of each of its fronts is
+// replaced by its inverse (partitioned inverse), so that the ORAS sweeps
+// become dependency-free dense products (sweep.cu).
 #include <algorithm>
 
 #include "common.h"
@@ -35,26 +41,30 @@ __global__ void front_assemble_kernel(const int32_t* __restrict__ level_fronts, 
         ws[amap_pos[q]] = from_d2<C>(B[amap_slot[q]]);
 }
 
-// child ci of every front of the level: parent[urel[b], urel[a]] += child[p_c + a, p_c + b], a >= b
+// child ci of every front of the level: parent[urel[a], urel[b]] += S_c[a, b], a >= b,
+// where S_c is the child's Schur block and the parent entry lies in its panel
+// (pivot column) or in its own Schur block.
 template <typename C>
 __global__ void extend_add_kernel(const int32_t* __restrict__ level_fronts, int lo, int ci,
                                   const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child,
                                   const int32_t* __restrict__ P, const int32_t* __restrict__ U,
-                                  const int64_t* __restrict__ f_off, const int64_t* __restrict__ u_off,
-                                  const int32_t* __restrict__ urel, C* __restrict__ ws) {
+                                  const int64_t* __restrict__ f_off, const int64_t* __restrict__ sch_off,
+                                  const int64_t* __restrict__ u_off, const int32_t* __restrict__ urel,
+                                  C* __restrict__ ws, const C* __restrict__ sch_child, C* __restrict__ sch_par) {
     const int s = level_fronts[lo + blockIdx.y];
     if (child_ptr[s] + ci >= child_ptr[s + 1]) return;
     const int c = child[child_ptr[s] + ci];
-    const int pc = P[c], uc = U[c];
-    const int64_t fc = (int64_t)pc + uc;
+    const int uc = U[c];
     const int b = blockIdx.x * blockDim.y + threadIdx.y;
     if (b >= uc) return;
-    const int64_t fs = (int64_t)P[s] + U[s];
+    const int ps = P[s], us = U[s];
+    const int64_t fs = (int64_t)ps + us;
     const int32_t* rel = urel + u_off[c];
-    const C* src = ws + f_off[c] + (pc + b) * fc + pc;
-    C* dst = ws + f_off[s] + (int64_t)rel[b] * fs;
+    const C* src = sch_child + sch_off[c] + (int64_t)b * uc;
+    const int rb = rel[b];
+    C* dst = rb < ps ? ws + f_off[s] + (int64_t)rb * fs : sch_par + sch_off[s] + (int64_t)(rb - ps) * us - ps;
     for (int a = b + threadIdx.x; a < uc; a += blockDim.x) {
-        C v = src[a];
+        const C v = src[a];
         C& d = dst[rel[a]];
         d.x += v.x;
         d.y += v.y;
@@ -137,7 +147,9 @@ __global__ void __launch_bounds__(256) panel_kernel(const int32_t* __restrict__ 
 template <typename C, int TILE, int NB>
 __global__ void __launch_bounds__(256) update_kernel(const int32_t* __restrict__ level_fronts, int lo, int k,
                                                      const int32_t* __restrict__ P, const int32_t* __restrict__ U,
-                                                     const int64_t* __restrict__ f_off, C* __restrict__ ws) {
+                                                     const int64_t* __restrict__ f_off,
+                                                     const int64_t* __restrict__ sch_off, C* __restrict__ ws,
+                                                     C* __restrict__ sch) {
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bj > bi) return;
     const int s = level_fronts[lo + blockIdx.z];
@@ -184,32 +196,141 @@ __global__ void __launch_bounds__(256) update_kernel(const int32_t* __restrict__
 #pragma unroll
             for (int b = 0; b < MT; ++b) acc[a][b] = cfma(av[a], bv[b], acc[a][b]);
     }
+    const int u = U[s];
+    C* S = sch + sch_off[s];
 #pragma unroll
     for (int b = 0; b < MT; ++b) {
         const int64_t col = rowB + ty + 16 * b;
         if (col >= f) continue;
+        // pivot columns live in the panel (ld f), the others in the Schur block (ld u)
+        C* colp = col < p ? F + col * f : S + (col - p) * u - p;
 #pragma unroll
         for (int a = 0; a < MT; ++a) {
             const int64_t row = rowA + tx + 16 * a;
             if (row < f && row >= col) {
-                C& dst = F[col * f + row];
+                C& dst = colp[row];
                 dst = csub(dst, acc[a][b]);
             }
         }
     }
 }
 
+// L11^{-1} for every front of a level (partitioned inverse used by the
+// sweeps): block (front, RC columns c0..) solves L11 X = I[:, c0:c0+RC] for
+// rows >= c0 by column-blocked forward substitution (warp-synchronous
+// triangles, row updates below), writing the strictly lower part of X to tmp.
+template <typename C, int RC>
+__global__ void __launch_bounds__(256) invert_l11_kernel(const int32_t* __restrict__ level_fronts, int lo,
+                                                         const int32_t* __restrict__ P, const int32_t* __restrict__ U,
+                                                         const int64_t* __restrict__ f_off,
+                                                         const int64_t* __restrict__ inv_off,
+                                                         const C* __restrict__ ws, C* __restrict__ tmp) {
+    constexpr int RP = RC + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* w = reinterpret_cast<C*>(smem_raw);
+    __shared__ C Ld[32][33];
+    const int s = level_fronts[lo + blockIdx.y];
+    const int p = P[s];
+    const int c0 = blockIdx.x * RC;
+    if (c0 >= p) return;
+    const int64_t f = (int64_t)p + U[s];
+    const C* L = ws + f_off[s];
+    C* T = tmp + inv_off[lo + blockIdx.y];
+    const int nr = p - c0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < nr * RC; e += 256) {
+        const int i = e / RC, r = e - i * RC;
+        w[i * RP + r] = (i == r) ? cmake<C>(1, 0) : czero<C>();
+    }
+    for (int jb = c0; jb < p; jb += 32) {
+        const int nb = min(32, p - jb);
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int i = e & 31, j = e >> 5;
+            Ld[i][j] = (i < nb && j < i) ? L[(int64_t)(jb + j) * f + jb + i] : czero<C>();
+        }
+        __syncthreads();
+        if (warp < RC) {
+            C val = lane < nb ? w[(jb - c0 + lane) * RP + warp] : czero<C>();
+            for (int j = 0; j < nb; ++j) {
+                C x;
+                x.x = __shfl_sync(0xffffffffu, val.x, j);
+                x.y = __shfl_sync(0xffffffffu, val.y, j);
+                val = cfms(Ld[lane][j], x, val);
+            }
+            if (lane < nb) w[(jb - c0 + lane) * RP + warp] = val;
+        }
+        __syncthreads();
+        for (int i = jb + nb + tid; i < p; i += 256) {
+            C acc[RC];
+#pragma unroll
+            for (int r = 0; r < RC; ++r) acc[r] = w[(i - c0) * RP + r];
+            for (int j = 0; j < nb; ++j) {
+                const C l = L[(int64_t)(jb + j) * f + i];
+                const C* wj = w + (jb + j - c0) * RP;
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[r] = cfms(l, wj[r], acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RC; ++r) w[(i - c0) * RP + r] = acc[r];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * RC; e += 256) {
+        const int i = e / RC, r = e - i * RC;
+        if (c0 + r < p && i > r) T[(int64_t)(c0 + r) * p + c0 + i] = w[i * RP + r];
+    }
+}
+
+template <typename C>
+__global__ void copy_linv_kernel(const int32_t* __restrict__ level_fronts, int lo, const int32_t* __restrict__ P,
+                                 const int32_t* __restrict__ U, const int64_t* __restrict__ f_off,
+                                 const int64_t* __restrict__ inv_off, const C* __restrict__ tmp, C* __restrict__ ws) {
+    const int s = level_fronts[lo + blockIdx.y];
+    const int p = P[s];
+    const int j = blockIdx.x;
+    if (j >= p) return;
+    const int64_t f = (int64_t)p + U[s];
+    C* L = ws + f_off[s];
+    const C* T = tmp + inv_off[lo + blockIdx.y];
+    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) L[(int64_t)j * f + i] = T[(int64_t)j * p + i];
+}
+
 template <typename C> struct FactorCfg;
 template <> struct FactorCfg<float2> { static constexpr int NB = 32; static constexpr int TILE = 64; };
 template <> struct FactorCfg<double2> { static constexpr int NB = 16; static constexpr int TILE = 32; };
 
+template <typename C, int RC>
+static void invert_level(const FrontsDev& F, int l, int lo, int nf, C* ws, C* tmp, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        MWI_CUDA(cudaFuncSetAttribute(invert_l11_kernel<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+        attr = true;
+    }
+    const int pmax = F.level_pmax[l];
+    const size_t sm = (size_t)pmax * (RC + 1) * sizeof(C);
+    MWI_REQUIRE(sm <= 200 * 1024, MWI_EINVAL, "front too large for the shared-memory inversion");
+    dim3 grd((pmax + RC - 1) / RC, nf);
+    invert_l11_kernel<C, RC><<<grd, 256, sm, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.f_off.p, F.inv_off.p, ws,
+                                                   tmp);
+    MWI_CHECK_LAUNCH();
+    copy_linv_kernel<C><<<dim3(pmax, nf), 128, 0, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.f_off.p, F.inv_off.p,
+                                                        tmp, ws);
+    MWI_CHECK_LAUNCH();
+}
+
 template <typename C>
-void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, int* perturbed, cudaStream_t st) {
+void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const sch[2], C* inv_tmp, int* perturbed,
+                      cudaStream_t st) {
     constexpr int NB = FactorCfg<C>::NB, TILE = FactorCfg<C>::TILE;
     MWI_CUDA(cudaMemsetAsync(ws, 0, (size_t)F.ws_entries * sizeof(C), st));
     const int nlev = (int)F.level_ptr.size() - 1;
     for (int l = 0; l < nlev; ++l) {
         const int lo0 = F.level_ptr[l], hi = F.level_ptr[l + 1];
+        C* sch_l = sch[l & 1];
+        const C* sch_child = sch[(l + 1) & 1];
+        if (F.level_sch[l] > 0) MWI_CUDA(cudaMemsetAsync(sch_l, 0, (size_t)F.level_sch[l] * sizeof(C), st));
         for (int lo = lo0; lo < hi; lo += 65535) {
             const int nf = std::min(65535, hi - lo);
             front_assemble_kernel<C><<<nf, 256, 0, st>>>(F.level_fronts.p, lo, F.amap_front_ptr.p, F.amap_slot.p,
@@ -222,7 +343,8 @@ void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, int* pert
                 dim3 grd((umax_child + 3) / 4, nf);
                 for (int ci = 0; ci < 2; ++ci) {
                     extend_add_kernel<C><<<grd, blk, 0, st>>>(F.level_fronts.p, lo, ci, F.child_ptr.p, F.child.p,
-                                                              F.p.p, F.u.p, F.f_off.p, F.u_off.p, F.urel.p, ws);
+                                                              F.p.p, F.u.p, F.f_off.p, F.sch_off.p, F.u_off.p,
+                                                              F.urel.p, ws, sch_child, sch_l);
                     MWI_CHECK_LAUNCH();
                 }
             }
@@ -236,14 +358,18 @@ void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, int* pert
                 if (nrem <= 0) continue;
                 const int T = (nrem + TILE - 1) / TILE;
                 update_kernel<C, TILE, NB><<<dim3(T, T, nf), 256, 0, st>>>(F.level_fronts.p, lo, k, F.p.p, F.u.p,
-                                                                           F.f_off.p, ws);
+                                                                           F.f_off.p, F.sch_off.p, ws, sch_l);
                 MWI_CHECK_LAUNCH();
             }
+            if (sizeof(C) == sizeof(float2)) invert_level<C, 8>(F, l, lo, nf, ws, inv_tmp, st);
+            else invert_level<C, 4>(F, l, lo, nf, ws, inv_tmp, st);
         }
     }
 }
 
-template void factorize_fronts<float2>(const FrontsDev&, const double2*, float2*, int*, cudaStream_t);
-template void factorize_fronts<double2>(const FrontsDev&, const double2*, double2*, int*, cudaStream_t);
+template void factorize_fronts<float2>(const FrontsDev&, const double2*, float2*, float2* const[2], float2*, int*,
+                                       cudaStream_t);
+template void factorize_fronts<double2>(const FrontsDev&, const double2*, double2*, double2* const[2], double2*,
+                                        int*, cudaStream_t);
 
 }  // namespace mwi

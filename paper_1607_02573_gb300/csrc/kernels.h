@@ -55,11 +55,19 @@ void launch_slot_fill(const SlotMatrixDev& S, const double* K, const double* M, 
                       int npack_f, const int32_t* fu_face, const double2* fu_coef, const double2* eps, double k0,
                       double2* out64, float2* out32, cudaStream_t st);
 
-// ---- multifrontal factorisation and ORAS application (factor.cu, oras.cu)
+// ---- multifrontal factorisation and ORAS application (factor.cu, sweep.cu, oras.cu)
+// GEMM tiles of the sweeps: (front, first row) per level, for pivot-row tiles
+// (FWD_P, BWD_T, BWD_X) and update-row tiles (FWD_U).
+struct TileLists {
+    int tm = 0;
+    DevBuf<int2> p_tiles, u_tiles;
+    std::vector<int64_t> p_ptr, u_ptr;  // [n_levels+1]
+};
+
 struct FrontsDev {
     int64_t nfronts = 0;
     DevBuf<int32_t> start, p, u, parent, sub;
-    DevBuf<int64_t> f_off, u_off, upd_row;
+    DevBuf<int64_t> f_off, u_off, upd_row, sch_off;
     DevBuf<int32_t> child_ptr, child;
     DevBuf<int32_t> urows, urel;
     DevBuf<int64_t> amap_front_ptr, amap_slot, amap_pos;
@@ -74,15 +82,27 @@ struct FrontsDev {
     DevBuf<int32_t> own_row;
     DevBuf<double> own_w;
     int64_t nloc = 0, upd_rows = 0, ws_entries = 0;
+    std::vector<int64_t> level_sch;    // host: sum u^2 of each level
+    int64_t sch_entries[2] = {0, 0};
     int n_sub = 0;
+    TileLists tiles64, tiles32;        // TM = 64 (complex FP32) / 32 (complex FP64)
+    DevBuf<int64_t> inv_off;           // per level position: offset of the front's p x p block
+    int64_t inv_entries = 0;           // largest sum of p^2 over a level
 };
 
+// ws: factor store (panels); sch[2]: transient Schur buffers (even / odd levels)
 template <typename C>
-void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, int* perturbed, cudaStream_t st);
+void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const sch[2], C* inv_tmp, int* perturbed,
+                      cudaStream_t st);
+
+// y = M^{-1} x; scratch: Y, Z [nloc][m], upd [upd_rows][m]
+template <typename C>
+void oras_apply(const FrontsDev& F, const C* ws, const double2* x, double2* y, int m, C* Y, C* Z, C* upd,
+                cudaStream_t st, const float2* x32 = nullptr, float2* y32 = nullptr);
 
 template <typename C>
-void oras_apply(const FrontsDev& F, const C* ws, const double2* x, double2* y, int m, C* Y, C* upd,
-                cudaStream_t st, const float2* x32 = nullptr, float2* y32 = nullptr);
+void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, cudaStream_t st);
+int sweep_tile_rows(bool fp32);
 
 // ---- Krylov building blocks (krylov.cu)
 template <typename C>

@@ -84,7 +84,8 @@ struct Front {
     int32_t u;        // update rows (ancestors' DOFs)
     int32_t parent;   // global front id or -1
     int32_t level;    // 0 = root level of its subdomain tree
-    int64_t f_off;    // offset of the f x f workspace (entries)
+    int64_t f_off;    // offset of the f x p panel [L11; L21] in the factor store (entries)
+    int64_t sch_off;  // offset of the u x u Schur block in its level's transient buffer
     int64_t u_off;    // offset into the concatenated U lists / relative maps
     int64_t upd_row;  // first row of this front's update vector in the solve buffer
 };
@@ -111,11 +112,25 @@ struct Decomposition {
     std::vector<int64_t> amap_slot;     // front assembly: source slot of B
     std::vector<int64_t> amap_pos;      // destination entry in the front workspace
     std::vector<int64_t> amap_front_ptr;  // [nfronts+1]
-    int64_t ws_entries = 0;             // total front workspace entries
+    int64_t ws_entries = 0;             // factor store entries (sum f * p)
+    std::vector<int64_t> level_sch;     // sum u^2 per level (Schur blocks, transient)
+    int64_t sch_entries[2] = {0, 0};    // transient Schur buffer size for even / odd levels
     int64_t upd_rows = 0;               // total update-vector rows
     int64_t factor_entries = 0;         // sum f * p
     double factor_flops = 0;            // real flops of the numeric factorisation
     int32_t max_front = 0;
+};
+
+// Result of the symbolic analysis of one subdomain (local front ids).
+struct LocalFront {
+    int32_t start, p, u, parent, level;
+    int64_t u_off;  // into LocalSymbolic::urows / urel
+};
+struct LocalSymbolic {
+    std::vector<int32_t> nd_order;   // nd_order[k] = natural index of ND position k
+    std::vector<LocalFront> fronts;  // children before parents
+    std::vector<int32_t> urows, urel;
+    double flops = 0;
 };
 
 void rcb_partition(const Topology& T, int nparts, std::vector<int32_t>& part);
@@ -124,11 +139,8 @@ void build_decomposition(const Topology& T, const int32_t* part_in, int n_sub, i
 void build_global_slots(const Topology& T, SlotMatrix& A, FaceUses& fu);
 // Nested-dissection ordering and multifrontal structure of one subdomain.
 // rows_glob: global DOF of each local row (natural order); adj: local graph
-// (natural numbering, no self loops).  Appends the subdomain's fronts to D and
-// returns nd_order[k] = natural index of the row at ND position k.
-void symbolic_subdomain(const Topology& T, Decomposition& D, int sub,
-                        const std::vector<int32_t>& rows_glob,
-                        const std::vector<std::vector<int32_t>>& adj,
-                        std::vector<int32_t>& nd_order);
+// (natural numbering, no self loops).
+void symbolic_subdomain(const Topology& T, int nd_leaf, const std::vector<int32_t>& rows_glob,
+                        const std::vector<std::vector<int32_t>>& adj, LocalSymbolic& out);
 
 }  // namespace mwi

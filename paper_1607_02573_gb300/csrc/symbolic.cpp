@@ -100,23 +100,21 @@ struct Ctx {
 
 }  // namespace
 
-void symbolic_subdomain(const Topology& T, Decomposition& D, int sub,
-                        const std::vector<int32_t>& rows_glob,
-                        const std::vector<std::vector<int32_t>>& adj,
-                        std::vector<int32_t>& nd_order) {
+void symbolic_subdomain(const Topology& T, int nd_leaf, const std::vector<int32_t>& rows_glob,
+                        const std::vector<std::vector<int32_t>>& adj, LocalSymbolic& out) {
     const int32_t n = (int32_t)rows_glob.size();
     Ctx C;
     C.T = &T;
     C.rows = &rows_glob;
     C.adj = &adj;
-    C.leaf = D.nd_leaf;
+    C.leaf = nd_leaf;
     C.nd_pos.assign(n, -1);
     C.side.assign(n, -1);
     std::vector<int32_t> all(n);
     std::iota(all.begin(), all.end(), 0);
     C.rec(all, 0);
-    nd_order.assign(n, -1);
-    for (int32_t v = 0; v < n; ++v) nd_order[C.nd_pos[v]] = v;
+    out.nd_order.assign(n, -1);
+    for (int32_t v = 0; v < n; ++v) out.nd_order[C.nd_pos[v]] = v;
 
     // update sets, children before parents (creation order is a postorder)
     std::vector<int32_t> buf;
@@ -125,7 +123,7 @@ void symbolic_subdomain(const Topology& T, Decomposition& D, int sub,
         buf.clear();
         for (int32_t v : s.piv)
             for (int32_t w : adj[v]) {
-                int32_t x = C.nd_pos[w];
+                const int32_t x = C.nd_pos[w];
                 if (x >= end) buf.push_back(x);
             }
         for (int32_t c : s.kids)
@@ -135,43 +133,37 @@ void symbolic_subdomain(const Topology& T, Decomposition& D, int sub,
         buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
         s.U = buf;
     }
-
-    // global fronts
-    const int32_t base = (int32_t)D.fronts.size();
-    for (size_t k = 0; k < C.nodes.size(); ++k) {
-        const Node& s = C.nodes[k];
-        Front F;
-        F.sub = sub;
+    out.fronts.clear();
+    out.urows.clear();
+    out.flops = 0;
+    for (const Node& s : C.nodes) {
+        LocalFront F;
         F.start = s.start;
         F.p = (int32_t)s.piv.size();
         F.u = (int32_t)s.U.size();
-        F.parent = s.parent >= 0 ? base + s.parent : -1;
+        F.parent = s.parent;
         F.level = s.depth;
+        F.u_off = (int64_t)out.urows.size();
+        out.urows.insert(out.urows.end(), s.U.begin(), s.U.end());
         const int64_t f = (int64_t)F.p + F.u;
-        F.f_off = D.ws_entries;
-        D.ws_entries += f * f;
-        F.u_off = (int64_t)D.urows.size();
-        F.upd_row = D.upd_rows;
-        D.upd_rows += F.u;
-        D.urows.insert(D.urows.end(), s.U.begin(), s.U.end());
-        D.factor_entries += f * F.p;
-        D.max_front = std::max<int32_t>(D.max_front, (int32_t)f);
         for (int64_t j = 0; j < F.p; ++j) {
-            double r = (double)(f - j - 1);
-            D.factor_flops += 8.0 * (r + 0.5 * r * (r + 1.0));
+            const double r = (double)(f - j - 1);
+            out.flops += 8.0 * (r + 0.5 * r * (r + 1.0));
         }
-        D.fronts.push_back(F);
+        out.fronts.push_back(F);
     }
     // relative positions of every child's update rows in its parent's front
-    D.urel.resize(D.urows.size(), -1);
+    out.urel.assign(out.urows.size(), -1);
     for (size_t k = 0; k < C.nodes.size(); ++k) {
         const Node& s = C.nodes[k];
-        if (s.parent < 0) continue;
+        if (s.parent < 0) {
+            MWI_REQUIRE(s.U.empty(), MWI_EINVAL, "internal: root front with update rows");
+            continue;
+        }
         const Node& P = C.nodes[s.parent];
-        const Front& Fc = D.fronts[base + k];
         const int32_t pend = P.start + (int32_t)P.piv.size();
         for (size_t j = 0; j < s.U.size(); ++j) {
-            int32_t x = s.U[j];
+            const int32_t x = s.U[j];
             int32_t pos;
             if (x < pend) {
                 MWI_REQUIRE(x >= P.start, MWI_EINVAL, "internal: update row below parent pivots");
@@ -181,12 +173,9 @@ void symbolic_subdomain(const Topology& T, Decomposition& D, int sub,
                 MWI_REQUIRE(it != P.U.end() && *it == x, MWI_EINVAL, "internal: update row not in parent");
                 pos = (int32_t)P.piv.size() + (int32_t)(it - P.U.begin());
             }
-            D.urel[Fc.u_off + j] = pos;
+            out.urel[out.fronts[k].u_off + j] = pos;
         }
     }
-    // every root front must have an empty update set
-    for (const Node& s : C.nodes)
-        if (s.parent < 0) MWI_REQUIRE(s.U.empty(), MWI_EINVAL, "internal: root front with update rows");
 }
 
 }  // namespace mwi
