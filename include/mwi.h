@@ -201,6 +201,27 @@ mwi_status mwi_spmm_device(mwi_problem_t prob, const double* x_dev, double* y_de
 mwi_status mwi_oras_apply_device(mwi_problem_t prob, const double* x_dev, double* y_dev,
                                  int32_t m);
 
+/* Allocation-free variant of mwi_oras_apply_device, for callers that cannot
+ * call cudaMalloc while they run: processes whose device memory is all handed
+ * to a pool allocator (for example PyTorch's caching allocator in a serving
+ * process that reserves the GPU up front), or latency-critical loops that must
+ * not pay cudaMalloc's implicit device synchronisation.  The paper has no
+ * counterpart; this is a deployment aid.
+ * Same arguments and result as mwi_oras_apply_device.  Its scratch (local
+ * vectors, update vectors, FP32 copies in the MIXED path) lives in one
+ * file-scope device array of 32 MiB that every GPU loading the library holds
+ * until the process exits; the call allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine).  A problem whose scratch need
+ * exceeds 32 MiB -- (2 * n_local + n_update_rows) * m complex values in the
+ * factor precision, plus 2 * n * m FP32 complex values when MIXED -- is
+ * rejected with MWI_EINVAL before any launch.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (different streams, threads or processes' contexts on one device) race and
+ * must be serialised by the caller. */
+mwi_status mwi_oras_apply_device_noalloc(mwi_problem_t prob, const double* x_dev, double* y_dev,
+                                         int32_t m);
+
 /* Global CSR of A: row_ptr [n+1] (host), col [nnz] (host), val [2*nnz] (host). */
 mwi_status mwi_matrix_csr(mwi_problem_t prob, int64_t* nnz, int64_t* row_ptr, int32_t* col,
                           double* val);

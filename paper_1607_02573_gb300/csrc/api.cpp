@@ -822,6 +822,17 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
     });
 }
 
+mwi_status mwi_oras_apply_device_noalloc(mwi_problem_t P, const double* x_dev, double* y_dev, int32_t m) {
+    return guard([&] {
+        MWI_REQUIRE(P && x_dev && y_dev && m >= 1, MWI_EINVAL, "bad argument");
+        DecompEntry& E = *P->dec;
+        const bool mixed = P->opts.precision == 1;
+        const void* ws = mixed ? (const void*)P->ws32.p : (const void*)P->ws64.p;
+        oras_apply_noalloc(E.F, ws, mixed, (const double2*)x_dev, (double2*)y_dev, m, P->mesh->T.ndof, P->st);
+        MWI_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
 mwi_status mwi_matrix_csr(mwi_problem_t P, int64_t* nnz, int64_t* row_ptr, int32_t* col, double* val) {
     return guard([&] {
         MWI_REQUIRE(P && nnz, MWI_EINVAL, "null argument");

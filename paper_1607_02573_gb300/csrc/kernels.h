@@ -104,6 +104,13 @@ template <typename C>
 void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, cudaStream_t st);
 int sweep_tile_rows(bool fp32);
 
+// Allocation-free ORAS application (oras.cu): scratch from a fixed-size
+// file-scope device array of kOrasScratchBytes.
+static const size_t kOrasScratchBytes = (size_t)32 << 20;
+size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed);
+void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const double2* x, double2* y, int m,
+                        int64_t n, cudaStream_t st);
+
 // ---- Krylov building blocks (krylov.cu)
 template <typename C>
 void spmm(int64_t n, const int32_t* row_ptr, const int32_t* col, const C* val, const C* x, C* y, int m,

@@ -11,6 +11,7 @@
 // Several right-hand sides go through one forward/backward sweep, as the
 // paper notes for multiple vectors (Section 3).  Vectors are row-major [rows][m].
 #include <algorithm>
+#include <mutex>
 
 #include "common.h"
 #include "gmres.h"
@@ -79,5 +80,74 @@ template void oras_apply<float2>(const FrontsDev&, const float2*, const double2*
                                  float2*, cudaStream_t, const float2*, float2*);
 template void oras_apply<double2>(const FrontsDev&, const double2*, const double2*, double2*, int, double2*,
                                   double2*, double2*, cudaStream_t, const float2*, float2*);
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the ORAS application.  Its scratch (the local
+// vectors Y and Z, the update vectors and, in the mixed path, the FP32 copies
+// of x and y) is carved from one file-scope device array of fixed size instead of
+// cudaMalloc'd buffers.  The array exists on every GPU that loads the library
+// until the process exits.  Host code cannot use the array's name as a device
+// address, so its address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// Every call shares the array and leaves its contents behind; nothing in it
+// needs to start at zero because the gather and the forward sweep write every
+// location before it is read.
+
+static __device__ __align__(256) unsigned char g_oras_scratch[kOrasScratchBytes];
+
+static void* oras_scratch_address() {
+    int dev = 0;
+    MWI_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::vector<void*> addr;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_oras_scratch);
+        if (e != cudaSuccess || !p)
+            throw Error(MWI_ECUDA, std::string("cudaGetSymbolAddress of the ORAS scratch failed: ") +
+                                       cudaGetErrorString(e));
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed) {
+    const size_t elt = mixed ? sizeof(float2) : sizeof(double2);
+    size_t b = 2 * round256((size_t)F.nloc * m * elt) + round256((size_t)std::max<int64_t>(1, F.upd_rows) * m * elt);
+    if (mixed) b += 2 * round256((size_t)n * m * sizeof(float2));
+    return b;
+}
+
+void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const double2* x, double2* y, int m,
+                        int64_t n, cudaStream_t st) {
+    const size_t need = oras_noalloc_bytes(F, n, m, mixed);
+    if (need > kOrasScratchBytes)
+        throw Error(MWI_EINVAL, "problem needs " + std::to_string(need) + " bytes of ORAS scratch; the "
+                                "allocation-free entry point holds " + std::to_string(kOrasScratchBytes));
+    unsigned char* base = static_cast<unsigned char*>(oras_scratch_address());
+    const size_t elt = mixed ? sizeof(float2) : sizeof(double2);
+    unsigned char* Yp = base;
+    unsigned char* Zp = Yp + round256((size_t)F.nloc * m * elt);
+    unsigned char* Up = Zp + round256((size_t)F.nloc * m * elt);
+    unsigned char* Vp = Up + round256((size_t)std::max<int64_t>(1, F.upd_rows) * m * elt);
+    unsigned char* Xp = Vp + round256((size_t)n * m * sizeof(float2));
+    if (mixed) {
+        float2* v32 = reinterpret_cast<float2*>(Vp);
+        float2* x32 = reinterpret_cast<float2*>(Xp);
+        convert_c128_to_c64(n * m, x, v32, st);
+        oras_apply_impl<float2, float2, float2>(F, static_cast<const float2*>(ws), v32, x32, m,
+                                                reinterpret_cast<float2*>(Yp), reinterpret_cast<float2*>(Zp),
+                                                reinterpret_cast<float2*>(Up), st);
+        convert_c64_to_c128(n * m, x32, y, st);
+    } else {
+        oras_apply_impl<double2, double2, double2>(F, static_cast<const double2*>(ws), x, y, m,
+                                                   reinterpret_cast<double2*>(Yp), reinterpret_cast<double2*>(Zp),
+                                                   reinterpret_cast<double2*>(Up), st);
+    }
+}
 
 }  // namespace mwi

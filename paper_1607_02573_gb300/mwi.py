@@ -72,6 +72,7 @@ _SIGS = {
     "mwi_problem_destroy": [_vp],
     "mwi_spmm_device": [_vp, _vp, _vp, C.c_int32],
     "mwi_oras_apply_device": [_vp, _vp, _vp, C.c_int32],
+    "mwi_oras_apply_device_noalloc": [_vp, _vp, _vp, C.c_int32],
     "mwi_matrix_csr": [_vp, _i64p, _i64p, _i32p, _dp],
     "mwi_decomposition": [_vp, _i32p, _i64p],
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
