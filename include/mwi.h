@@ -86,6 +86,8 @@ typedef struct {
     int32_t verbose;      /* 0 silent, 1 phase timings on stderr [0] */
     const int32_t* part;  /* optional [nt] host array: caller's tet -> subdomain map
                              (values in [0, n_sub)); NULL = recursive coordinate bisection */
+    int32_t max_block;    /* right-hand sides per block solve; more transmitters are solved in
+                             blocks of this width (Krylov memory grows with it) [64] */
 } mwi_solver_opts;
 
 typedef struct {

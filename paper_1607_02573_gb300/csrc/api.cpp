@@ -74,7 +74,7 @@ struct mwi_problem {
     DevBuf<float2> Y32, Z32, upd32;
     Gmres<double2> outer;
     Gmres<float2> inner;
-    DevBuf<double2> U, Lam, Brhs, R;
+    DevBuf<double2> U, Lam, Brhs, R, Bc, Xc;
     DevBuf<float2> v32, x32, r32;
     DevBuf<double> dscratch;
     int m_fwd = 0;
@@ -141,6 +141,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     if (d.inner_iters <= 0) d.inner_iters = 30;
     if (d.inner_rtol <= 0) d.inner_rtol = 1e-4;
     if (d.nd_leaf <= 0) d.nd_leaf = 64;
+    if (d.max_block <= 0) d.max_block = 64;
     return d;
 }
 
@@ -263,6 +264,7 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     up(F.f_off, f_off, st); up(F.u_off, u_off, st); up(F.upd_row, upd_row, st); up(F.sch_off, sch_off, st);
     up(F.child_ptr, D.child_ptr, st); up(F.child, D.child, st);
     up(F.urows, D.urows, st); up(F.urel, D.urel, st);
+    up(F.asm_base, D.asm_base, st); up(F.asm_ptr, D.asm_ptr, st); up(F.asm_src, D.asm_src, st);
     up(F.amap_front_ptr, D.amap_front_ptr, st); up(F.amap_slot, D.amap_slot, st); up(F.amap_pos, D.amap_pos, st);
     up(F.level_fronts, D.level_fronts, st);
     F.level_ptr = D.level_ptr;
@@ -449,6 +451,48 @@ void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<in
 }
 
 // solve A X = B for m columns by FGMRES; returns info
+void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info);
+
+// solve A X = B for m columns in blocks of at most opts.max_block columns
+// (Krylov bases scale with the block width); X and B are [n][m]
+void solve_columns(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
+    const int mb = P->opts.max_block;
+    if (m <= mb) {
+        solve_block(P, B, X, m, info);
+        return;
+    }
+    const int64_t n = P->mesh->T.ndof;
+    cudaStream_t st = P->st;
+    P->Bc.ensure((size_t)n * mb);
+    P->Xc.ensure((size_t)n * mb);
+    mwi_solve_info tot;
+    std::memset(&tot, 0, sizeof(tot));
+    bool notconv = false;
+    for (int c0 = 0; c0 < m; c0 += mb) {
+        const int mc = std::min(mb, m - c0);
+        copy_columns(n, m, c0, mc, B, mc, 0, P->Bc.p, st);
+        mwi_solve_info ci;
+        std::memset(&ci, 0, sizeof(ci));
+        try {
+            solve_block(P, P->Bc.p, P->Xc.p, mc, &ci);
+        } catch (const Error& e) {
+            if (e.status != MWI_ENOTCONV) throw;
+            notconv = true;
+        }
+        copy_columns(n, mc, 0, mc, P->Xc.p, m, c0, X, st);
+        tot.iters_max = std::max(tot.iters_max, ci.iters_max);
+        tot.inner_total += ci.inner_total;
+        tot.n_converged += ci.n_converged;
+        tot.n_perturbed = ci.n_perturbed;
+        tot.resid_max = std::max(tot.resid_max, ci.resid_max);
+        tot.setup_ms = ci.setup_ms;
+        tot.solve_ms += ci.solve_ms;
+    }
+    MWI_CUDA(cudaStreamSynchronize(st));
+    if (info) *info = tot;
+    if (notconv) throw Error(MWI_ENOTCONV, "FGMRES did not reach rtol on every column");
+}
+
 void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
     mwi_mesh* M = P->mesh;
     const int64_t n = M->T.ndof;
@@ -457,7 +501,8 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     const mwi_solver_opts& o = P->opts;
     const bool mixed = o.precision == 1;
     DecompEntry& E = *P->dec;
-    const int restart = std::min(o.restart, std::max(1, o.max_iter));
+    // the mixed path's outer FGMRES needs few steps: keep its FP64 bases short
+    const int restart = std::min(mixed ? std::min(o.restart, 12) : o.restart, std::max(1, o.max_iter));
     P->outer.reserve(n, m, restart);
     P->R.ensure(nm);
     P->dscratch.ensure(4 * (size_t)m);
@@ -655,7 +700,7 @@ mwi_status mwi_forward_solve(mwi_problem_t P, const mwi_antenna* tx, int32_t n_t
         P->m_fwd = m;
         P->n_rx = n_rx;
         try {
-            solve_block(P, P->Brhs.p, P->U.p, m, info);
+            solve_columns(P, P->Brhs.p, P->U.p, m, info);
         } catch (const Error& e) {
             if (e.status != MWI_ENOTCONV) throw;
             status = MWI_ENOTCONV;
@@ -699,7 +744,7 @@ static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const 
         launch_adjoint_rhs(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->r_d.p, wd, P->Brhs.p, st);
         P->Lam.ensure(nm);
         try {
-            solve_block(P, P->Brhs.p, P->Lam.p, m, info);
+            solve_columns(P, P->Brhs.p, P->Lam.p, m, info);
         } catch (const Error& e) {
             if (e.status != MWI_ENOTCONV) throw;
             status = MWI_ENOTCONV;

@@ -489,6 +489,30 @@ void build_decomposition(const Topology& T, const int32_t* part_in, int n_sub, i
         for (int64_t k = 0; k < nfr; ++k)
             if (D.fronts[k].parent >= 0) D.child[fill[D.fronts[k].parent]++] = (int32_t)k;
     }
+    // gather lists of the sweeps' extend-add
+    D.asm_base.assign(nfr, 0);
+    int64_t rows = 0;
+    for (int64_t k = 0; k < nfr; ++k) {
+        D.asm_base[k] = rows;
+        rows += (int64_t)D.fronts[k].p + D.fronts[k].u;
+    }
+    D.asm_ptr.assign(rows + 1, 0);
+    for (int64_t k = 0; k < nfr; ++k)
+        for (int32_t q = D.child_ptr[k]; q < D.child_ptr[k + 1]; ++q) {
+            const Front& C = D.fronts[D.child[q]];
+            for (int32_t j = 0; j < C.u; ++j) D.asm_ptr[D.asm_base[k] + D.urel[C.u_off + j] + 1]++;
+        }
+    for (int64_t r = 0; r < rows; ++r) D.asm_ptr[r + 1] += D.asm_ptr[r];
+    D.asm_src.assign(D.asm_ptr[rows], 0);
+    {
+        std::vector<int64_t> fill(D.asm_ptr.begin(), D.asm_ptr.end() - 1);
+        for (int64_t k = 0; k < nfr; ++k)
+            for (int32_t q = D.child_ptr[k]; q < D.child_ptr[k + 1]; ++q) {
+                const Front& C = D.fronts[D.child[q]];
+                for (int32_t j = 0; j < C.u; ++j)
+                    D.asm_src[fill[D.asm_base[k] + D.urel[C.u_off + j]]++] = (int32_t)(C.upd_row + j);
+            }
+    }
 }
 
 }  // namespace mwi

@@ -7,7 +7,7 @@
 
 namespace mwi {
 
-static const int kDotBlocks = 304;  // 2 x 152 SMs
+static const int kDotBlocks = 608;  // 4 x 152 SMs
 
 // y = op(x) on [n][m] device vectors
 template <typename C>
@@ -39,5 +39,8 @@ void convert_c128_to_c64(int64_t nm, const double2* a, float2* b, cudaStream_t s
 void convert_c64_to_c128(int64_t nm, const float2* a, double2* b, cudaStream_t st);
 void residual_c128(int64_t nm, const double2* b, double2* r, cudaStream_t st);  // r = b - r
 void tolerances(int m, const double* b2, double rtol, double* tol, double* bnorm, cudaStream_t st);
+// dst[r][dc0 + c] = src[r][sc0 + c] for c < mc (row-major [n][ms] -> [n][md])
+void copy_columns(int64_t n, int ms, int sc0, int mc, const double2* src, int md, int dc0, double2* dst,
+                  cudaStream_t st);
 
 }  // namespace mwi

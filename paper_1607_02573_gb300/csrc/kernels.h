@@ -70,6 +70,8 @@ struct FrontsDev {
     DevBuf<int64_t> f_off, u_off, upd_row, sch_off;
     DevBuf<int32_t> child_ptr, child;
     DevBuf<int32_t> urows, urel;
+    DevBuf<int64_t> asm_base, asm_ptr;   // gather lists of the sweeps' extend-add
+    DevBuf<int32_t> asm_src;
     DevBuf<int64_t> amap_front_ptr, amap_slot, amap_pos;
     DevBuf<int32_t> level_fronts;
     std::vector<int32_t> level_ptr;   // host copy

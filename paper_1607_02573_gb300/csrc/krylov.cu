@@ -56,7 +56,9 @@ template void spmm<float2>(int64_t, const int32_t*, const int32_t*, const float2
                            cudaStream_t);
 
 // ---------------------------------------------------------------- dots
-// partial[b][i][c] = sum over this block's rows of conj(V_i[r][c]) W[r][c]
+// partial[b][i][c] = sum over this block's rows of conj(V_i[r][c]) W[r][c].
+// Rows are visited four at a time with independent loads, so that enough
+// memory requests are in flight to stream V and W at HBM rate.
 template <typename C>
 __global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec, const C* __restrict__ V,
                                                    int64_t vstride, const C* __restrict__ W,
@@ -64,16 +66,37 @@ __global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec, c
     __shared__ double2 red[8][8][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = blockIdx.y * 32 + tx;
+    const int64_t stride = (int64_t)gridDim.x * 8;
     for (int i0 = 0; i0 < nvec; i0 += 8) {
+        const int nq = min(8, nvec - i0);
         C acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = czero<C>();
         if (c < m) {
-            for (int64_t r = blockIdx.x * 8 + ty; r < n; r += (int64_t)gridDim.x * 8) {
+            int64_t r = blockIdx.x * 8 + ty;
+            for (; r + 3 * stride < n; r += 4 * stride) {
+                C w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) w[u] = W[(r + u * stride) * m + c];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < nq) {
+                        const C* Vq = V + (int64_t)(i0 + q) * vstride + c;
+                        C v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v[u] = Vq[(r + u * stride) * m];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            acc[q].x += v[u].x * w[u].x + v[u].y * w[u].y;
+                            acc[q].y += v[u].x * w[u].y - v[u].y * w[u].x;
+                        }
+                    }
+            }
+            for (; r < n; r += stride) {
                 const C w = W[r * m + c];
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (i0 + q < nvec) {
+                    if (q < nq) {
                         const C v = V[(int64_t)(i0 + q) * vstride + r * m + c];
                         acc[q].x += v.x * w.x + v.y * w.y;
                         acc[q].y += v.x * w.y - v.y * w.x;
@@ -383,6 +406,21 @@ void residual_c128(int64_t nm, const double2* b, double2* r, cudaStream_t st) {
     sub_from_kernel<double2><<<nblocks(nm, 256), 256, 0, st>>>(nm, b, r);
     MWI_CHECK_LAUNCH();
 }
+__global__ void copy_columns_kernel(int64_t n, int ms, int sc0, int mc, const double2* __restrict__ src, int md,
+                                    int dc0, double2* __restrict__ dst) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * mc) return;
+    const int64_t r = e / mc;
+    const int c = (int)(e - r * mc);
+    dst[r * md + dc0 + c] = src[r * ms + sc0 + c];
+}
+
+void copy_columns(int64_t n, int ms, int sc0, int mc, const double2* src, int md, int dc0, double2* dst,
+                  cudaStream_t st) {
+    copy_columns_kernel<<<nblocks(n * mc, 256), 256, 0, st>>>(n, ms, sc0, mc, src, md, dc0, dst);
+    MWI_CHECK_LAUNCH();
+}
+
 void tolerances(int m, const double* b2, double rtol, double* tol, double* bnorm, cudaStream_t st) {
     tol_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, b2, rtol, tol, bnorm);
     MWI_CHECK_LAUNCH();

@@ -108,6 +108,12 @@ struct Decomposition {
     int n_levels = 0;
     std::vector<int32_t> child_ptr, child;  // children of every front
     std::vector<int32_t> urows;         // [sum u] U lists (local ND index)
+    // gather form of the update-vector extend-add of the sweeps: for front
+    // row t of front s (index asm_base[s] + t), the rows of the children's
+    // update vectors that add into it, children ascending
+    std::vector<int64_t> asm_base;      // [nfronts] first front-row index of each front
+    std::vector<int64_t> asm_ptr;       // [sum f + 1]
+    std::vector<int32_t> asm_src;       // [sum u] row in the update buffer
     std::vector<int32_t> urel;          // [sum u] position of U_c[k] in the parent's front
     std::vector<int64_t> amap_slot;     // front assembly: source slot of B
     std::vector<int64_t> amap_pos;      // destination entry in the front workspace

@@ -44,6 +44,9 @@ struct FrontArgs {
     const int32_t* child_ptr;
     const int32_t* child;
     const int32_t* urel;
+    const int64_t* asm_base;
+    const int64_t* asm_ptr;
+    const int32_t* asm_src;
 };
 
 template <typename C, int MODE>
@@ -194,31 +197,31 @@ __global__ void __launch_bounds__(256) sweep_gemm_kernel(const int2* __restrict_
     }
 }
 
-// w_P = Y[P] + children's updates (in place in Y), w_U = children's updates.
-template <typename C>
-__global__ void __launch_bounds__(256) sweep_assemble_kernel(const int32_t* __restrict__ level_fronts, int lo,
-                                                             FrontArgs fa, C* __restrict__ Y, C* __restrict__ upd,
-                                                             int m) {
-    const int s = level_fronts[lo + blockIdx.x];
+// Extend-add of the children's update vectors in gather form, tiled like the
+// GEMMs: w_P = Y[P] + children's rows (in place in Y), w_U = children's rows
+// (into the front's own update vector).  Every front row sums its sources in
+// a fixed order (children ascending), so no atomics are needed.
+template <typename C, bool UPART>
+__global__ void __launch_bounds__(256) sweep_gather_kernel(const int2* __restrict__ tiles, int tm, FrontArgs fa,
+                                                           C* __restrict__ Y, C* __restrict__ upd, int m) {
+    const int2 tile = tiles[blockIdx.x];
+    const int s = tile.x, row0 = tile.y;
     const int p = fa.P[s], u = fa.U[s];
+    const int nrows = min(tm, (UPART ? u : p) - row0);
+    const int c = blockIdx.y * 32 + (threadIdx.x & 31);
+    if (c >= m) return;
     const int64_t rowbase = fa.sub_off[fa.sub[s]] + fa.start[s];
-    C* us = upd + fa.upd_row[s] * m;
-    for (int64_t e = threadIdx.x; e < (int64_t)u * m; e += blockDim.x) us[e] = czero<C>();
-    __syncthreads();
-    for (int q = fa.child_ptr[s]; q < fa.child_ptr[s + 1]; ++q) {
-        const int c = fa.child[q];
-        const int uc = fa.U[c];
-        const int32_t* rel = fa.urel + fa.u_off[c];
-        const C* src = upd + fa.upd_row[c] * m;
-        for (int64_t e = threadIdx.x; e < (int64_t)uc * m; e += blockDim.x) {
-            const int k = (int)(e / m), col = (int)(e - (int64_t)k * m);
-            const int t = rel[k];
-            const C v = src[e];
-            C& d = t < p ? Y[(rowbase + t) * m + col] : us[(int64_t)(t - p) * m + col];
-            d.x += v.x;
-            d.y += v.y;
+    const int64_t base = fa.asm_base[s] + (UPART ? p : 0) + row0;
+    for (int i = threadIdx.x >> 5; i < nrows; i += 8) {
+        const int t = row0 + i;
+        C acc = UPART ? czero<C>() : Y[(rowbase + t) * m + c];
+        for (int64_t q = fa.asm_ptr[base + i]; q < fa.asm_ptr[base + i + 1]; ++q) {
+            const C v = upd[(int64_t)fa.asm_src[q] * m + c];
+            acc.x += v.x;
+            acc.y += v.y;
         }
-        __syncthreads();
+        if (UPART) upd[(fa.upd_row[s] + t) * m + c] = acc;
+        else Y[(rowbase + t) * m + c] = acc;
     }
 }
 
@@ -237,6 +240,9 @@ static FrontArgs front_args(const FrontsDev& F) {
     a.child_ptr = F.child_ptr.p;
     a.child = F.child.p;
     a.urel = F.urel.p;
+    a.asm_base = F.asm_base.p;
+    a.asm_ptr = F.asm_ptr.p;
+    a.asm_src = F.asm_src.p;
     return a;
 }
 
@@ -257,14 +263,22 @@ static void launch_gemm(const FrontsDev& F, const TileLists& T, int l, const C* 
     }
 }
 
+template <typename C, bool UPART>
+static void launch_gather(const FrontsDev& F, const TileLists& T, int l, C* Y, C* upd, int m, cudaStream_t st) {
+    const int64_t b = UPART ? T.u_ptr[l] : T.p_ptr[l];
+    const int64_t e = UPART ? T.u_ptr[l + 1] : T.p_ptr[l + 1];
+    if (e <= b) return;
+    const int2* tiles = (UPART ? T.u_tiles.p : T.p_tiles.p) + b;
+    dim3 grd((unsigned)(e - b), (unsigned)((m + 31) / 32));
+    sweep_gather_kernel<C, UPART><<<grd, 256, 0, st>>>(tiles, T.tm, front_args<C>(F), Y, upd, m);
+    MWI_CHECK_LAUNCH();
+}
+
 template <typename C>
 void sweep_forward_level(const FrontsDev& F, const TileLists& T, int l, const C* ws, C* Y, C* Z, C* upd, int m,
                          cudaStream_t st) {
-    for (int lo = F.level_ptr[l]; lo < F.level_ptr[l + 1]; lo += 65535) {
-        const int nf = std::min(65535, F.level_ptr[l + 1] - lo);
-        sweep_assemble_kernel<C><<<nf, 256, 0, st>>>(F.level_fronts.p, lo, front_args<C>(F), Y, upd, m);
-        MWI_CHECK_LAUNCH();
-    }
+    launch_gather<C, false>(F, T, l, Y, upd, m, st);
+    launch_gather<C, true>(F, T, l, Y, upd, m, st);
     launch_gemm<C, 0>(F, T, l, ws, Y, Z, upd, m, st);
     launch_gemm<C, 1>(F, T, l, ws, Y, Z, upd, m, st);
 }

@@ -168,3 +168,21 @@ def test_order2_forward_and_gradient_parity(lib, precision, rtol, tol):
     assert abs(J - J_o) <= tol * abs(J_o)
     assert rel_err(grad, grad_o) <= tol
     P.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_columns_independent_of_block_width(lib, precision):
+    """Every right-hand side keeps its own Krylov state, so a column's result is the
+    same (bit for bit) whether it is solved alone, in a block of 3 or in one block."""
+    case = chamber_case(12, 11, n_ant=8)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    res = []
+    for mb in (64, 3, 1):
+        P = lib.Problem(M, eps, FREQ, n_sub=4, precision=precision, rtol=1e-9, max_block=mb)
+        S = P.forward_solve(tx, rx)
+        J, grad = P.misfit_and_gradient(S * 0.9)
+        res.append((S, J, grad))
+        P.close()
+    for S, J, grad in res[1:]:
+        assert np.array_equal(S, res[0][0])
+        assert np.array_equal(grad, res[0][2])
