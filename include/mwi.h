@@ -78,10 +78,14 @@ typedef struct {
     int32_t restart;      /* outer FGMRES restart length [50] */
     int32_t n_sub;        /* ORAS subdomains N_S [64] */
     int32_t overlap;      /* overlap delta in vertex-adjacent tet layers [1]; < 0 means none */
-    int32_t precision;    /* 0 = complex FP64 everywhere; 1 = MIXED: complex FP32 subdomain
-                             factors and inner GMRES inside FP64 outer FGMRES [0] */
-    int32_t inner_iters;  /* MIXED: inner GMRES iterations per outer step [30] */
-    double inner_rtol;    /* MIXED: inner relative residual target [1e-4] */
+    int32_t precision;    /* 0 = complex FP64 everywhere;
+                             1 = MIXED: complex FP32 subdomain factors and ORAS application as
+                                 the preconditioner of the FP64 FGMRES (Arnoldi, residuals,
+                                 least squares in FP64);
+                             2 = MIXED_NESTED: an inner complex FP32 GMRES(ORAS) as the flexible
+                                 preconditioner of the FP64 FGMRES [0] */
+    int32_t inner_iters;  /* MIXED_NESTED: inner GMRES iterations per outer step [30] */
+    double inner_rtol;    /* MIXED_NESTED: inner relative residual target [1e-4] */
     int32_t nd_leaf;      /* nested-dissection leaf size of the subdomain ordering [64] */
     int32_t verbose;      /* 0 silent, 1 phase timings on stderr [0] */
     const int32_t* part;  /* optional [nt] host array: caller's tet -> subdomain map
@@ -92,7 +96,7 @@ typedef struct {
 
 typedef struct {
     int32_t iters_max;    /* largest outer iteration count over columns */
-    int32_t inner_total;  /* MIXED: inner iterations summed over outer steps */
+    int32_t inner_total;  /* MIXED_NESTED: inner iterations summed over outer steps */
     int32_t n_converged;  /* columns whose true relative residual <= rtol */
     int32_t n_perturbed;  /* pivots perturbed in the factorisation */
     double resid_max;     /* largest true relative residual over columns */

@@ -341,10 +341,11 @@ void numeric_setup(mwi_problem* P) {
     P->A_coef.ensure(std::max<size_t>(1, M->A_fu.face.size()));
     launch_face_coef(M->A_fu_tet.p, (int64_t)M->A_fu.face.size(), P->eps.p, P->k0, P->A_coef.p, st);
     P->Aval.ensure(M->A.nnz);
-    const bool mixed = P->opts.precision == 1;
-    if (mixed) P->Aval32.ensure(M->A.nnz);
+    const bool mixed = P->opts.precision != 0;
+    const bool nested = P->opts.precision == 2;
+    if (nested) P->Aval32.ensure(M->A.nnz);
     launch_slot_fill(M->A, M->Kp.p, M->Mp.p, M->tabs.npack, M->Bf.p, M->tabs.npack_f, M->A_fu_face.p, P->A_coef.p,
-                     P->eps.p, P->k0, P->Aval.p, mixed ? P->Aval32.p : nullptr, st);
+                     P->eps.p, P->k0, P->Aval.p, nested ? P->Aval32.p : nullptr, st);
     DecompEntry& E = *P->dec;
     P->B_coef.ensure(std::max<size_t>(1, E.D.B_faces.face.size()));
     launch_face_coef(E.fu_tet.p, (int64_t)E.D.B_faces.face.size(), P->eps.p, P->k0, P->B_coef.p, st);
@@ -383,7 +384,7 @@ void create_problem(mwi_mesh* M, const double* eps, bool eps_dev, double freq, c
     MWI_REQUIRE(freq > 0 && std::isfinite(freq), MWI_EINVAL, "frequency must be positive");
     std::unique_ptr<mwi_problem> P(new mwi_problem());
     P->opts = defaults(opts);
-    MWI_REQUIRE(P->opts.precision == 0 || P->opts.precision == 1, MWI_EINVAL, "precision must be 0 or 1");
+    MWI_REQUIRE(P->opts.precision >= 0 && P->opts.precision <= 2, MWI_EINVAL, "precision must be 0, 1 or 2");
     MWI_REQUIRE(P->opts.n_sub <= M->T.nt, MWI_EINVAL, "more subdomains than tets");
     P->mesh = M;
     P->st = (cudaStream_t)stream;
@@ -499,10 +500,11 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     const int64_t nm = n * m;
     cudaStream_t st = P->st;
     const mwi_solver_opts& o = P->opts;
-    const bool mixed = o.precision == 1;
+    const bool mixed = o.precision != 0;
+    const bool nested = o.precision == 2;
     DecompEntry& E = *P->dec;
-    // the mixed path's outer FGMRES needs few steps: keep its FP64 bases short
-    const int restart = std::min(mixed ? std::min(o.restart, 12) : o.restart, std::max(1, o.max_iter));
+    // with an inner GMRES the outer FGMRES needs few steps: keep its FP64 bases short
+    const int restart = std::min(nested ? std::min(o.restart, 12) : o.restart, std::max(1, o.max_iter));
     P->outer.reserve(n, m, restart);
     P->R.ensure(nm);
     P->dscratch.ensure(4 * (size_t)m);
@@ -515,7 +517,7 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
         P->Y32.ensure((size_t)E.F.nloc * m);
         P->Z32.ensure((size_t)E.F.nloc * m);
         P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
-        P->inner.reserve(n, m, std::max(1, o.inner_iters));
+        if (nested) P->inner.reserve(n, m, std::max(1, o.inner_iters));
         P->v32.ensure(nm);
         P->x32.ensure(nm);
     } else {
@@ -541,8 +543,14 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
             });
             return;
         }
-        // inner GMRES in complex FP32 on A z = x, preconditioned by the FP32 ORAS
         convert_c128_to_c64(nm, x, P->v32.p, st);
+        if (!nested) {
+            // the complex FP32 ORAS itself is the preconditioner of the FP64 FGMRES
+            M32(P->v32.p, P->x32.p);
+            convert_c64_to_c128(nm, P->x32.p, y, st);
+            return;
+        }
+        // inner GMRES in complex FP32 on A z = x, preconditioned by the FP32 ORAS
         MWI_CUDA(cudaMemsetAsync(P->x32.p, 0, nm * sizeof(float2), st));
         double* vb2 = P->inner.dvec.p + 5 * m;
         double* tin = P->inner.dvec.p + 6 * m;
@@ -846,7 +854,7 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
         MWI_REQUIRE(P && x_dev && y_dev && m >= 1, MWI_EINVAL, "bad argument");
         DecompEntry& E = *P->dec;
         const int64_t n = P->mesh->T.ndof;
-        if (P->opts.precision == 1) {
+        if (P->opts.precision != 0) {
             P->Y32.ensure((size_t)E.F.nloc * m);
             P->Z32.ensure((size_t)E.F.nloc * m);
             P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
@@ -871,7 +879,7 @@ mwi_status mwi_oras_apply_device_noalloc(mwi_problem_t P, const double* x_dev, d
     return guard([&] {
         MWI_REQUIRE(P && x_dev && y_dev && m >= 1, MWI_EINVAL, "bad argument");
         DecompEntry& E = *P->dec;
-        const bool mixed = P->opts.precision == 1;
+        const bool mixed = P->opts.precision != 0;
         const void* ws = mixed ? (const void*)P->ws32.p : (const void*)P->ws64.p;
         oras_apply_noalloc(E.F, ws, mixed, (const double2*)x_dev, (double2*)y_dev, m, P->mesh->T.ndof, P->st);
         MWI_CUDA(cudaStreamSynchronize(P->st));

@@ -90,7 +90,7 @@ def test_oras_apply_parity(lib, precision, tol):
 
 
 @pytest.mark.parametrize("case_name", ["cube", "chamber"])
-@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6)])
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6), (2, 1e-9, 1e-6)])
 def test_forward_and_gradient_parity(lib, case_name, precision, rtol, tol):
     case = cube_case(8) if case_name == "cube" else chamber_case(16, 15)
     mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
@@ -170,7 +170,7 @@ def test_order2_forward_and_gradient_parity(lib, precision, rtol, tol):
     P.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_columns_independent_of_block_width(lib, precision):
     """Every right-hand side keeps its own Krylov state, so a column's result is the
     same (bit for bit) whether it is solved alone, in a block of 3 or in one block."""
