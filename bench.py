@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--n-ant", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nd-leaf", type=int, default=64)
+    ap.add_argument("--engine", type=int, default=1, help="complex FP32 sweep engine (see mwi_solver_opts)")
     return ap.parse_args()
 
 
@@ -135,7 +136,7 @@ def run_mine(args, rank, world):
 
     def one_arm(precision, steps, warmup, e2e_steps):
         P = mwi.Problem(M, eps_d, FREQ, stream=stream, n_sub=64, precision=precision, rtol=RTOL,
-                        verbose=2, max_iter=500, nd_leaf=args.nd_leaf)
+                        verbose=2, max_iter=500, nd_leaf=args.nd_leaf, sweep_engine=args.engine)
         fs = P.factor_stats()
         # synthetic measurements: S of the two-inclusion target map plus 1 % noise
         from synthetic import add_noise, chamber_target_eps

@@ -92,6 +92,10 @@ typedef struct {
                              (values in [0, n_sub)); NULL = recursive coordinate bisection */
     int32_t max_block;    /* right-hand sides per block solve; more transmitters are solved in
                              blocks of this width (Krylov memory grows with it) [64] */
+    int32_t sweep_engine; /* MIXED modes, engine of the complex FP32 ORAS sweeps:
+                             0 = default (1); 1 = tensor cores, operands split into two TF32
+                             parts (about FP32 accuracy); 2 = tensor cores, plain TF32;
+                             3 = CUDA cores, FP32 */
 } mwi_solver_opts;
 
 typedef struct {

@@ -142,6 +142,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     if (d.inner_rtol <= 0) d.inner_rtol = 1e-4;
     if (d.nd_leaf <= 0) d.nd_leaf = 64;
     if (d.max_block <= 0) d.max_block = 64;
+    if (d.sweep_engine <= 0) d.sweep_engine = 1;
     return d;
 }
 
@@ -155,6 +156,9 @@ cudaEvent_t take_event(mwi_problem* P) {
     MWI_CUDA(cudaEventCreate(&e));
     return e;
 }
+
+// complex FP32 sweep engine: 0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores TF32
+int tc_of(const mwi_solver_opts& o) { return o.sweep_engine == 3 ? 0 : o.sweep_engine; }
 
 // timed region helper: records an event pair around fn when enabled
 template <typename Fn>
@@ -272,13 +276,22 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     F.level_pmax.assign(nlev, 0);
     F.level_fmax.assign(nlev, 0);
     F.level_umax.assign(nlev, 0);
+    F.level_pmean.assign(nlev, 0.0);
+    F.level_umean.assign(nlev, 0.0);
     for (int l = 0; l < nlev; ++l)
         for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
             const Front& fr = D.fronts[D.level_fronts[q]];
             F.level_pmax[l] = std::max(F.level_pmax[l], fr.p);
             F.level_fmax[l] = std::max(F.level_fmax[l], fr.p + fr.u);
             F.level_umax[l] = std::max(F.level_umax[l], fr.u);
+            F.level_pmean[l] += fr.p;
+            F.level_umean[l] += fr.u;
         }
+    for (int l = 0; l < nlev; ++l) {
+        const double cnt = std::max(1, D.level_ptr[l + 1] - D.level_ptr[l]);
+        F.level_pmean[l] /= cnt;
+        F.level_umean[l] /= cnt;
+    }
     up(F.sub_off, D.sub_off, st);
     up(F.loc2glob, D.loc2glob, st);
     up(F.own_ptr, D.own_ptr, st);
@@ -385,6 +398,7 @@ void create_problem(mwi_mesh* M, const double* eps, bool eps_dev, double freq, c
     std::unique_ptr<mwi_problem> P(new mwi_problem());
     P->opts = defaults(opts);
     MWI_REQUIRE(P->opts.precision >= 0 && P->opts.precision <= 2, MWI_EINVAL, "precision must be 0, 1 or 2");
+    MWI_REQUIRE(P->opts.sweep_engine >= 1 && P->opts.sweep_engine <= 3, MWI_EINVAL, "sweep_engine must be 0..3");
     MWI_REQUIRE(P->opts.n_sub <= M->T.nt, MWI_EINVAL, "more subdomains than tets");
     P->mesh = M;
     P->st = (cudaStream_t)stream;
@@ -533,7 +547,8 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     };
     auto M32 = [&](const float2* x, float2* y) {
         timed(P, 1, [&] {
-            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, x, y);
+            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, x, y,
+                               tc_of(P->opts));
         });
     };
     auto M64 = [&](const double2* x, double2* y) {
@@ -862,7 +877,7 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
             P->x32.ensure(n * m);
             convert_c128_to_c64(n * m, (const double2*)x_dev, P->v32.p, P->st);
             oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, P->st, P->v32.p,
-                               P->x32.p);
+                               P->x32.p, tc_of(P->opts));
             convert_c64_to_c128(n * m, P->x32.p, (double2*)y_dev, P->st);
         } else {
             P->Y64.ensure((size_t)E.F.nloc * m);
@@ -881,7 +896,8 @@ mwi_status mwi_oras_apply_device_noalloc(mwi_problem_t P, const double* x_dev, d
         DecompEntry& E = *P->dec;
         const bool mixed = P->opts.precision != 0;
         const void* ws = mixed ? (const void*)P->ws32.p : (const void*)P->ws64.p;
-        oras_apply_noalloc(E.F, ws, mixed, (const double2*)x_dev, (double2*)y_dev, m, P->mesh->T.ndof, P->st);
+        oras_apply_noalloc(E.F, ws, mixed, (const double2*)x_dev, (double2*)y_dev, m, P->mesh->T.ndof, P->st,
+                           tc_of(P->opts));
         MWI_CUDA(cudaStreamSynchronize(P->st));
     });
 }

@@ -31,8 +31,13 @@ struct Gmres {
     // residual <= tol[c] (device array).  Returns steps taken.
     int cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const double* tol, int max_steps,
               cudaStream_t st, double* resid_host, int* iters_used);
-    void dots(const C* V, int nvec, int64_t vstride, const C* w, double2* out, double2* acc, cudaStream_t st);
+    // out[i][c] = conj(V_i)^T w (i < nvec), plus conj(w)^T w at i = nvec when self = 1;
+    // acc[i] += out[i] for i < nvec
+    void dots(const C* V, int nvec, int64_t vstride, const C* w, double2* out, double2* acc, cudaStream_t st,
+              int self = 0);
     void column_norms2(const C* x, double* out, cudaStream_t st);
+    void column_norms2_into(const C* x, double* out, double2* tmp, cudaStream_t st);
+    int reorth_passes = 0;
 };
 
 void convert_c128_to_c64(int64_t nm, const double2* a, float2* b, cudaStream_t st);

@@ -87,7 +87,8 @@ struct FrontsDev {
     std::vector<int64_t> level_sch;    // host: sum u^2 of each level
     int64_t sch_entries[2] = {0, 0};
     int n_sub = 0;
-    TileLists tiles64, tiles32;        // TM = 64 (complex FP32) / 32 (complex FP64)
+    TileLists tiles64, tiles32;        // 64-row and 32-row tiles of every level
+    std::vector<double> level_pmean, level_umean;  // host: mean p and u of each level
     DevBuf<int64_t> inv_off;           // per level position: offset of the front's p x p block
     int64_t inv_entries = 0;           // largest sum of p^2 over a level
 };
@@ -97,13 +98,14 @@ template <typename C>
 void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const sch[2], C* inv_tmp, int* perturbed,
                       cudaStream_t st);
 
-// y = M^{-1} x; scratch: Y, Z [nloc][m], upd [upd_rows][m]
+// y = M^{-1} x; scratch: Y, Z [nloc][m], upd [upd_rows][m]; tc selects the
+// complex FP32 sweep engine (0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores TF32)
 template <typename C>
 void oras_apply(const FrontsDev& F, const C* ws, const double2* x, double2* y, int m, C* Y, C* Z, C* upd,
-                cudaStream_t st, const float2* x32 = nullptr, float2* y32 = nullptr);
+                cudaStream_t st, const float2* x32 = nullptr, float2* y32 = nullptr, int tc = 0);
 
 template <typename C>
-void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, cudaStream_t st);
+void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, int tc, cudaStream_t st);
 int sweep_tile_rows(bool fp32);
 
 // Allocation-free ORAS application (oras.cu): scratch from a fixed-size
@@ -111,7 +113,7 @@ int sweep_tile_rows(bool fp32);
 static const size_t kOrasScratchBytes = (size_t)32 << 20;
 size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed);
 void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const double2* x, double2* y, int m,
-                        int64_t n, cudaStream_t st);
+                        int64_t n, cudaStream_t st, int tc = 0);
 
 // ---- Krylov building blocks (krylov.cu)
 template <typename C>

@@ -59,14 +59,16 @@ template void spmm<float2>(int64_t, const int32_t*, const int32_t*, const float2
 // partial[b][i][c] = sum over this block's rows of conj(V_i[r][c]) W[r][c].
 // Rows are visited four at a time with independent loads, so that enough
 // memory requests are in flight to stream V and W at HBM rate.
+// With self = 1 the product conj(W) W is appended as vector index nvec.
 template <typename C>
-__global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec, const C* __restrict__ V,
-                                                   int64_t vstride, const C* __restrict__ W,
+__global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec_in, const C* __restrict__ V,
+                                                   int64_t vstride, const C* __restrict__ W, int self,
                                                    double2* __restrict__ partial) {
     __shared__ double2 red[8][8][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c = blockIdx.y * 32 + tx;
     const int64_t stride = (int64_t)gridDim.x * 8;
+    const int nvec = nvec_in + self;
     for (int i0 = 0; i0 < nvec; i0 += 8) {
         const int nq = min(8, nvec - i0);
         C acc[8];
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec, c
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
                     if (q < nq) {
-                        const C* Vq = V + (int64_t)(i0 + q) * vstride + c;
+                        const C* Vq = (i0 + q < nvec_in ? V + (int64_t)(i0 + q) * vstride : W) + c;
                         C v[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) v[u] = Vq[(r + u * stride) * m];
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec, c
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
                     if (q < nq) {
-                        const C v = V[(int64_t)(i0 + q) * vstride + r * m + c];
+                        const C v = (i0 + q < nvec_in ? V + (int64_t)(i0 + q) * vstride : W)[r * m + c];
                         acc[q].x += v.x * w.x + v.y * w.y;
                         acc[q].y += v.x * w.y - v.y * w.x;
                     }
@@ -121,8 +123,8 @@ __global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec, c
     }
 }
 
-// h[i][c] (+)= sum_b partial[b][i][c]
-__global__ void dots_reduce_kernel(int nblk, int nvec, int m, const double2* __restrict__ partial,
+// h[i][c] = sum_b partial[b][i][c] for i < nvec; hacc[i][c] += h[i][c] for i < nacc
+__global__ void dots_reduce_kernel(int nblk, int nvec, int nacc, int m, const double2* __restrict__ partial,
                                    double2* __restrict__ h, double2* __restrict__ hacc) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nvec * m) return;
@@ -133,7 +135,15 @@ __global__ void dots_reduce_kernel(int nblk, int nvec, int m, const double2* __r
         s.y += v.y;
     }
     h[e] = s;
-    if (hacc) { hacc[e].x += s.x; hacc[e].y += s.y; }
+    if (hacc && e < nacc * m) { hacc[e].x += s.x; hacc[e].y += s.y; }
+}
+
+// any column whose norm fell below half of its value before the projection
+__global__ void reorth_test_kernel(int m, const double2* __restrict__ w0sq, const double* __restrict__ w1sq,
+                                   int* __restrict__ flag) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    if (w1sq[c] < 0.5 * w0sq[c].x) atomicOr(flag, 1);
 }
 
 // W[r][c] -= sum_i V_i[r][c] h[i][c]
@@ -300,6 +310,7 @@ void Gmres<C>::reserve(int64_t n_, int m_, int restart_) {
     m = m_;
     restart = restart_;
     V.ensure((size_t)(restart + 1) * n * m);
+    reorth_passes = 0;
     Z.ensure((size_t)restart * n * m);
     W.ensure((size_t)n * m);
     H.ensure((size_t)restart * (restart + 1) * m);
@@ -307,27 +318,34 @@ void Gmres<C>::reserve(int64_t n_, int m_, int restart_) {
     sn.ensure((size_t)restart * m);
     g.ensure((size_t)(restart + 1) * m);
     y.ensure((size_t)restart * m);
-    h.ensure((size_t)(restart + 1) * m);
+    h.ensure((size_t)(restart + 2) * m);
     hacc.ensure((size_t)(restart + 1) * m);
-    partial.ensure((size_t)kDotBlocks * (restart + 1) * m);
+    partial.ensure((size_t)kDotBlocks * (restart + 2) * m);
     dvec.ensure((size_t)8 * m);
     ivec.ensure((size_t)4 * m + 4);
 }
 
 template <typename C>
 void Gmres<C>::dots(const C* Vb, int nvec, int64_t vstride, const C* w, double2* out, double2* acc,
-                    cudaStream_t st) {
+                    cudaStream_t st, int self) {
     dim3 blk(32, 8), grd(kDotBlocks, (m + 31) / 32);
-    dots_kernel<C><<<grd, blk, 0, st>>>(n, m, nvec, Vb, vstride, w, partial.p);
+    dots_kernel<C><<<grd, blk, 0, st>>>(n, m, nvec, Vb, vstride, w, self, partial.p);
     MWI_CHECK_LAUNCH();
-    dots_reduce_kernel<<<nblocks((int64_t)nvec * m, 128), 128, 0, st>>>(kDotBlocks, nvec, m, partial.p, out, acc);
+    const int nt = nvec + self;
+    dots_reduce_kernel<<<nblocks((int64_t)nt * m, 128), 128, 0, st>>>(kDotBlocks, nt, nvec, m, partial.p, out, acc);
     MWI_CHECK_LAUNCH();
 }
 
 template <typename C>
 void Gmres<C>::column_norms2(const C* x, double* out, cudaStream_t st) {
-    dots(x, 1, 0, x, h.p, nullptr, st);
-    real_part_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, h.p, out);
+    column_norms2_into(x, out, h.p, st);
+}
+
+// ||x_c||^2 with tmp [m] double2 scratch
+template <typename C>
+void Gmres<C>::column_norms2_into(const C* x, double* out, double2* tmp, cudaStream_t st) {
+    dots(x, 0, 0, x, tmp, nullptr, st, 1);
+    real_part_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, tmp, out);
     MWI_CHECK_LAUNCH();
 }
 
@@ -343,6 +361,7 @@ int Gmres<C>::cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const doubl
     int* active = ivec.p;
     int* kcol = ivec.p + m;
     int* nact = ivec.p + 4 * m;
+    int* flag = ivec.p + 4 * m + 1;
     column_norms2(r0, beta2, st);
     cycle_start_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, beta2, tol, active, kcol, g.p, inv, resid);
     MWI_CHECK_LAUNCH();
@@ -355,15 +374,29 @@ int Gmres<C>::cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const doubl
         C* zk = Z.p + (int64_t)k * vs;
         M(vk, zk);
         A(zk, W.p);
-        // CGS2
+        // classical Gram-Schmidt with selective reorthogonalisation: the second
+        // pass runs when some column lost more than half of its squared norm
+        // in the first (the usual twice-is-enough criterion)
         auto ortho = [&] {
             MWI_CUDA(cudaMemsetAsync(hacc.p, 0, (size_t)(k + 1) * m * sizeof(double2), st));
-            for (int pass = 0; pass < 2; ++pass) {
-                dots(V.p, k + 1, vs, W.p, h.p, hacc.p, st);
+            dots(V.p, k + 1, vs, W.p, h.p, hacc.p, st, 1);
+            const double2* w0sq = h.p + (int64_t)(k + 1) * m;
+            cgs_update_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, k + 1, V.p, vs, h.p, W.p);
+            MWI_CHECK_LAUNCH();
+            column_norms2_into(W.p, hn2, h.p + (int64_t)(k + 2) * m, st);
+            MWI_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+            reorth_test_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, w0sq, hn2, flag);
+            MWI_CHECK_LAUNCH();
+            int again = 0;
+            MWI_CUDA(cudaMemcpyAsync(&again, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MWI_CUDA(cudaStreamSynchronize(st));
+            if (again) {
+                ++reorth_passes;
+                dots(V.p, k + 1, vs, W.p, h.p, hacc.p, st, 0);
                 cgs_update_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, k + 1, V.p, vs, h.p, W.p);
                 MWI_CHECK_LAUNCH();
+                column_norms2(W.p, hn2, st);
             }
-            column_norms2(W.p, hn2, st);
         };
         if (timer) timer(2, ortho);
         else ortho();
