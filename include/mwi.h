@@ -93,9 +93,10 @@ typedef struct {
     int32_t max_block;    /* right-hand sides per block solve; more transmitters are solved in
                              blocks of this width (Krylov memory grows with it) [64] */
     int32_t sweep_engine; /* MIXED modes, engine of the complex FP32 ORAS sweeps:
-                             0 = default (1); 1 = tensor cores, operands split into two TF32
-                             parts (about FP32 accuracy); 2 = tensor cores, plain TF32;
-                             3 = CUDA cores, FP32 */
+                             0 = default (2); 1 = tensor cores, operands split into two TF32
+                             parts (about FP32 accuracy); 2 = tensor cores, plain TF32 (the
+                             preconditioner carries ~1e-3 relative rounding, absorbed by the
+                             outer FGMRES); 3 = CUDA cores, FP32 */
 } mwi_solver_opts;
 
 typedef struct {

@@ -74,6 +74,8 @@ struct mwi_problem {
     DevBuf<float2> Y32, Z32, upd32;
     Gmres<double2> outer;
     Gmres<float2> inner;
+    GmresDF dfk;                         // MIXED: double-float FGMRES
+    DevBuf<float2> Adf, Bdf, Xdf, Rdf;   // double-float planes
     DevBuf<double2> U, Lam, Brhs, R, Bc, Xc;
     DevBuf<float2> v32, x32, r32;
     DevBuf<double> dscratch;
@@ -142,7 +144,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     if (d.inner_rtol <= 0) d.inner_rtol = 1e-4;
     if (d.nd_leaf <= 0) d.nd_leaf = 64;
     if (d.max_block <= 0) d.max_block = 64;
-    if (d.sweep_engine <= 0) d.sweep_engine = 1;
+    if (d.sweep_engine <= 0) d.sweep_engine = 2;
     return d;
 }
 
@@ -359,6 +361,10 @@ void numeric_setup(mwi_problem* P) {
     if (nested) P->Aval32.ensure(M->A.nnz);
     launch_slot_fill(M->A, M->Kp.p, M->Mp.p, M->tabs.npack, M->Bf.p, M->tabs.npack_f, M->A_fu_face.p, P->A_coef.p,
                      P->eps.p, P->k0, P->Aval.p, nested ? P->Aval32.p : nullptr, st);
+    if (mixed && !nested) {
+        P->Adf.ensure(2 * (size_t)M->A.nnz);
+        split_c128(M->A.nnz, P->Aval.p, P->Adf.p, st);
+    }
     DecompEntry& E = *P->dec;
     P->B_coef.ensure(std::max<size_t>(1, E.D.B_faces.face.size()));
     launch_face_coef(E.fu_tet.p, (int64_t)E.D.B_faces.face.size(), P->eps.p, P->k0, P->B_coef.p, st);
@@ -467,6 +473,7 @@ void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<in
 
 // solve A X = B for m columns by FGMRES; returns info
 void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info);
+void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info);
 
 // solve A X = B for m columns in blocks of at most opts.max_block columns
 // (Krylov bases scale with the block width); X and B are [n][m]
@@ -516,6 +523,10 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     const mwi_solver_opts& o = P->opts;
     const bool mixed = o.precision != 0;
     const bool nested = o.precision == 2;
+    if (mixed && !nested) {
+        solve_block_df(P, B, X, m, info);
+        return;
+    }
     DecompEntry& E = *P->dec;
     // with an inner GMRES the outer FGMRES needs few steps: keep its FP64 bases short
     const int restart = std::min(nested ? std::min(o.restart, 12) : o.restart, std::max(1, o.max_iter));
@@ -616,6 +627,86 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     if (info) {
         info->iters_max = total;
         info->inner_total = P->inner_total;
+        info->n_converged = nconv;
+        info->n_perturbed = P->n_perturbed;
+        info->resid_max = rmax;
+        info->setup_ms = P->setup_ms;
+        info->solve_ms = now_ms() - t0;
+    }
+    if (nconv < m) throw Error(MWI_ENOTCONV, "FGMRES did not reach rtol on every column");
+}
+
+// MIXED: the complex FP32 ORAS preconditions an FGMRES whose basis, residual
+// and iterate are double-float planes (FP64-quality results on the FP32 pipes)
+void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
+    mwi_mesh* M = P->mesh;
+    const int64_t n = M->T.ndof;
+    const int64_t nm = n * m;
+    const int64_t nnz = M->A.nnz;
+    cudaStream_t st = P->st;
+    const mwi_solver_opts& o = P->opts;
+    DecompEntry& E = *P->dec;
+    const int restart = std::min(o.restart, std::max(1, o.max_iter));
+    GmresDF& G = P->dfk;
+    G.reserve(n, m, restart);
+    P->Bdf.ensure(2 * (size_t)nm);
+    P->Xdf.ensure(2 * (size_t)nm);
+    P->Rdf.ensure(2 * (size_t)nm);
+    P->dscratch.ensure(4 * (size_t)m);
+    double* b2 = P->dscratch.p;
+    double* tol = P->dscratch.p + m;
+    double* bnorm = P->dscratch.p + 2 * m;
+    double* r2 = P->dscratch.p + 3 * m;
+    P->Y32.ensure((size_t)E.F.nloc * m);
+    P->Z32.ensure((size_t)E.F.nloc * m);
+    P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+    auto Aop = [&](const float2* z, float2* w) {
+        timed(P, 0, [&] { spmm_df(n, M->A.row_ptr.p, M->A.col.p, P->Adf.p, nnz, z, w, m, st); });
+    };
+    auto Mop = [&](const float2* v, float2* z) {
+        timed(P, 1, [&] {
+            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, v, z,
+                               tc_of(P->opts));
+        });
+    };
+    G.timer = [P](int slot, const std::function<void()>& fn) { timed(P, slot, fn); };
+    const double t0 = now_ms();
+    split_c128(nm, B, P->Bdf.p, st);
+    G.norms2(P->Bdf.p, b2, st);
+    tolerances(m, b2, o.rtol, tol, bnorm, st);
+    std::vector<double> bn(m), rn(m);
+    MWI_CUDA(cudaMemcpyAsync(bn.data(), bnorm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MWI_CUDA(cudaMemsetAsync(P->Xdf.p, 0, 2 * nm * sizeof(float2), st));
+    MWI_CUDA(cudaMemcpyAsync(P->Rdf.p, P->Bdf.p, 2 * nm * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    int total = 0;
+    while (true) {
+        int used = 0;
+        G.cycle(Aop, Mop, P->Rdf.p, P->Xdf.p, tol, std::min(restart, o.max_iter - total), st, &used);
+        total += used;
+        // true residual in double-float
+        timed(P, 0, [&] {
+            residual_df(n, M->A.row_ptr.p, M->A.col.p, P->Adf.p, nnz, P->Bdf.p, P->Xdf.p, P->Rdf.p, m, st);
+        });
+        G.norms2(P->Rdf.p, r2, st);
+        MWI_CUDA(cudaMemcpyAsync(rn.data(), r2, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+        bool done = true;
+        for (int c = 0; c < m; ++c)
+            if (bn[c] > 0 && std::sqrt(std::max(rn[c], 0.0)) > o.rtol * bn[c]) done = false;
+        if (done || total >= o.max_iter || used == 0) break;
+    }
+    join_c128(nm, P->Xdf.p, X, st);
+    int nconv = 0;
+    double rmax = 0;
+    for (int c = 0; c < m; ++c) {
+        double rel = bn[c] > 0 ? std::sqrt(std::max(rn[c], 0.0)) / bn[c] : 0.0;
+        rmax = std::max(rmax, rel);
+        if (rel <= o.rtol) nconv++;
+    }
+    MWI_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        info->iters_max = total;
+        info->inner_total = 0;
         info->n_converged = nconv;
         info->n_perturbed = P->n_perturbed;
         info->resid_max = rmax;

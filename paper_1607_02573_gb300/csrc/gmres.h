@@ -37,8 +37,45 @@ struct Gmres {
               int self = 0);
     void column_norms2(const C* x, double* out, cudaStream_t st);
     void column_norms2_into(const C* x, double* out, double2* tmp, cudaStream_t st);
-    int reorth_passes = 0;
 };
+
+// FGMRES whose FP64-quality vectors (basis V, w, residual, iterate) are
+// double-float planes (hi [n][m] float2 followed by lo [n][m] float2) and
+// whose preconditioned directions Z are complex FP32 (the preconditioner's
+// own output, so stored exactly).  Arnoldi relation, residual and iterate
+// carry about 48 significant bits on the FP32 pipes; the Gram-Schmidt
+// coefficients are formed from the FP32 heads.
+struct GmresDF {
+    // w = A z (z exact in FP32, w double-float planes)
+    typedef std::function<void(const float2*, float2*)> OpA;
+    // z = M v (v: FP32 head plane of a basis vector, z complex FP32)
+    typedef std::function<void(const float2*, float2*)> OpM;
+    int64_t n = 0;
+    int m = 0, restart = 0;
+    DevBuf<float2> V, Z, W;
+    DevBuf<float4> hdf, ydf;
+    DevBuf<float2> invdf;
+    DevBuf<double2> H, cs, sn, g, y, h, hacc, partial;
+    DevBuf<double> dvec;
+    DevBuf<int> ivec;
+    std::function<void(int, const std::function<void()>&)> timer;
+
+    void reserve(int64_t n, int m, int restart);
+    // one cycle from the double-float residual r0, x (double-float) updated in place
+    int cycle(const OpA& A, const OpM& M, const float2* r0, float2* x, const double* tol, int max_steps,
+              cudaStream_t st, int* iters_used);
+    // ||x_c||^2 from the FP32 head plane
+    void norms2(const float2* xh, double* out, cudaStream_t st);
+};
+
+// w = A z with A as double-float planes (hi nnz entries, then lo), z complex FP32
+void spmm_df(int64_t n, const int32_t* row_ptr, const int32_t* col, const float2* A, int64_t nnz, const float2* z,
+             float2* w, int m, cudaStream_t st);
+// r = b - A x, all double-float
+void residual_df(int64_t n, const int32_t* row_ptr, const int32_t* col, const float2* A, int64_t nnz, const float2* b,
+                 const float2* x, float2* r, int m, cudaStream_t st);
+void split_c128(int64_t count, const double2* a, float2* out, cudaStream_t st);
+void join_c128(int64_t count, const float2* in, double2* a, cudaStream_t st);
 
 void convert_c128_to_c64(int64_t nm, const double2* a, float2* b, cudaStream_t st);
 void convert_c64_to_c128(int64_t nm, const float2* a, double2* b, cudaStream_t st);

@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "df.h"
 #include "gmres.h"
 #include "kernels.h"
 
@@ -123,9 +124,10 @@ __global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec_in
     }
 }
 
-// h[i][c] = sum_b partial[b][i][c] for i < nvec; hacc[i][c] += h[i][c] for i < nacc
+// h[i][c] = sum_b partial[b][i][c] for i < nvec; hacc[i][c] += h[i][c] for i < nacc;
+// hdf (optional) receives h as double-floats (re hi, re lo, im hi, im lo)
 __global__ void dots_reduce_kernel(int nblk, int nvec, int nacc, int m, const double2* __restrict__ partial,
-                                   double2* __restrict__ h, double2* __restrict__ hacc) {
+                                   double2* __restrict__ h, double2* __restrict__ hacc, float4* __restrict__ hdf) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nvec * m) return;
     double2 s = make_double2(0.0, 0.0);
@@ -136,15 +138,13 @@ __global__ void dots_reduce_kernel(int nblk, int nvec, int nacc, int m, const do
     }
     h[e] = s;
     if (hacc && e < nacc * m) { hacc[e].x += s.x; hacc[e].y += s.y; }
+    if (hdf) {
+        const float2 a = df_split(s.x), b = df_split(s.y);
+        hdf[e] = make_float4(a.x, a.y, b.x, b.y);
+    }
 }
 
-// any column whose norm fell below half of its value before the projection
-__global__ void reorth_test_kernel(int m, const double2* __restrict__ w0sq, const double* __restrict__ w1sq,
-                                   int* __restrict__ flag) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
-    if (w1sq[c] < 0.5 * w0sq[c].x) atomicOr(flag, 1);
-}
+
 
 // W[r][c] -= sum_i V_i[r][c] h[i][c]
 template <typename C>
@@ -220,10 +220,15 @@ __global__ void arnoldi_kernel(int m, int k, int restart, const double2* __restr
                                const double* __restrict__ hnorm2, double2* __restrict__ H,
                                double2* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ g,
                                int* __restrict__ active, int* __restrict__ kcol, const double* __restrict__ tol,
-                               double* __restrict__ resid, double* __restrict__ inv_norm, int* __restrict__ n_active) {
+                               double* __restrict__ resid, double* __restrict__ inv_norm, int* __restrict__ n_active,
+                               float2* __restrict__ inv_df) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
-    if (!active[c]) { inv_norm[c] = 0.0; return; }
+    if (!active[c]) {
+        inv_norm[c] = 0.0;
+        if (inv_df) inv_df[c] = make_float2(0.f, 0.f);
+        return;
+    }
     double2* Hk = H + (int64_t)k * (restart + 1) * m;
     for (int i = 0; i <= k; ++i) Hk[i * m + c] = h[i * m + c];
     const double hn = sqrt(fmax(hnorm2[c], 0.0));
@@ -250,13 +255,15 @@ __global__ void arnoldi_kernel(int m, int k, int restart, const double2* __restr
     const double rr = sqrt(cabs2(g[(k + 1) * m + c]));
     resid[c] = rr;
     inv_norm[c] = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (inv_df) inv_df[c] = df_split(inv_norm[c]);
     if (rr <= tol[c] || hn == 0.0 || !(rr == rr)) active[c] = 0;
     else atomicAdd(n_active, 1);
 }
 
 // y = R^{-1} g per column (R = rotated Hessenberg, kcol[c] columns)
+// ydf (optional) receives y as double-floats (re hi, re lo, im hi, im lo)
 __global__ void lsq_kernel(int m, int restart, const double2* __restrict__ H, const double2* __restrict__ g,
-                           const int* __restrict__ kcol, double2* __restrict__ y) {
+                           const int* __restrict__ kcol, double2* __restrict__ y, float4* __restrict__ ydf) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     const int kk = kcol[c];
@@ -268,12 +275,19 @@ __global__ void lsq_kernel(int m, int restart, const double2* __restrict__ H, co
         double2 d = H[((int64_t)i * (restart + 1) + i) * m + c];
         y[i * m + c] = (d.x == 0.0 && d.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(s, d);
     }
+    if (ydf)
+        for (int i = 0; i < restart; ++i) {
+            const double2 v = y[i * m + c];
+            const float2 a = df_split(v.x), b = df_split(v.y);
+            ydf[i * m + c] = make_float4(a.x, a.y, b.x, b.y);
+        }
 }
 
 // start of a cycle: g = (beta, 0, ...), inv = 1/beta, active = beta > tol
 __global__ void cycle_start_kernel(int m, const double* __restrict__ beta2, const double* __restrict__ tol,
                                    int* __restrict__ active, int* __restrict__ kcol, double2* __restrict__ g,
-                                   double* __restrict__ inv_norm, double* __restrict__ resid) {
+                                   double* __restrict__ inv_norm, double* __restrict__ resid,
+                                   float2* __restrict__ inv_df) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     const double b = sqrt(fmax(beta2[c], 0.0));
@@ -283,6 +297,7 @@ __global__ void cycle_start_kernel(int m, const double* __restrict__ beta2, cons
     const bool act = b > tol[c];
     active[c] = act ? 1 : 0;
     inv_norm[c] = act ? 1.0 / b : 0.0;
+    if (inv_df) inv_df[c] = df_split(inv_norm[c]);
 }
 
 __global__ void tol_kernel(int m, const double* __restrict__ b2, double rtol, double* __restrict__ tol,
@@ -301,6 +316,152 @@ __global__ void real_part_kernel(int m, const double2* __restrict__ h, double* _
     out[c] = h[c].x;
 }
 
+
+// ---------------------------------------------------------------- double-float vectors
+// A double-float [n][m] complex vector is two float2 planes, hi at p and lo at
+// p + n m (value = hi + lo per real component).
+
+// W = A Z (Z exact in FP32, RES = false) or W = B - A X (X and B double-float,
+// RES = true), A as double-float planes (Ah, Al); G lanes per row over columns
+template <int G, bool RES>
+__global__ void __launch_bounds__(256) spmm_df_kernel(int64_t n, const int32_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ col, const float2* __restrict__ Ah,
+                                                      const float2* __restrict__ Al, const float2* __restrict__ Xh,
+                                                      const float2* __restrict__ Xl, const float2* __restrict__ Bh,
+                                                      const float2* __restrict__ Bl, float2* __restrict__ Wh,
+                                                      float2* __restrict__ Wl, int m) {
+    const int lane = threadIdx.x % G;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    if (row >= n) return;
+    const int b = rp[row], e = rp[row + 1];
+    for (int c0 = 0; c0 < m; c0 += G) {
+        const int c = c0 + lane;
+        if (c >= m) break;
+        dfl re = {0.f, 0.f}, im = {0.f, 0.f};
+        if constexpr (RES) {
+            const float2 bh = Bh[row * m + c], bl = Bl[row * m + c];
+            re = dfl{bh.x, bl.x};
+            im = dfl{bh.y, bl.y};
+        }
+        for (int q = b; q < e; ++q) {
+            const float2 ah = Ah[q], al = Al[q];
+            const int64_t xi = (int64_t)col[q] * m + c;
+            const float2 xh = Xh[xi];
+            if constexpr (RES) {
+                const float2 xl = Xl[xi];
+                df_mac(re, -ah.x, -al.x, xh.x, xl.x);
+                df_mac(re, ah.y, al.y, xh.y, xl.y);
+                df_mac(im, -ah.x, -al.x, xh.y, xl.y);
+                df_mac(im, -ah.y, -al.y, xh.x, xl.x);
+            } else {
+                df_mac1(re, xh.x, ah.x, al.x);
+                df_mac1(re, -xh.y, ah.y, al.y);
+                df_mac1(im, xh.y, ah.x, al.x);
+                df_mac1(im, xh.x, ah.y, al.y);
+            }
+        }
+        re = df_norm(re);
+        im = df_norm(im);
+        Wh[row * m + c] = make_float2(re.h, im.h);
+        Wl[row * m + c] = make_float2(re.l, im.l);
+    }
+}
+
+// W -= sum_i V_i h_i per column (V_i and W double-float, h double-float
+// [nvec][m] as (re hi, re lo, im hi, im lo)); four basis vectors per step so
+// that their loads are in flight together
+__global__ void __launch_bounds__(256) cgs_update_df_kernel(int64_t nm, int m, int nvec, const float2* __restrict__ V,
+                                                            int64_t vstride, const float4* __restrict__ hdf,
+                                                            float2* __restrict__ W) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nm) return;
+    const int c = (int)(e % m);
+    const float2 wh = W[e], wl = W[nm + e];
+    dfl re = {wh.x, wl.x}, im = {wh.y, wl.y};
+    int i = 0;
+    for (; i + 4 <= nvec; i += 4) {
+        float2 vh[4], vl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            vh[u] = V[(int64_t)(i + u) * vstride + e];
+            vl[u] = V[(int64_t)(i + u) * vstride + nm + e];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 h = hdf[(i + u) * m + c];
+            df_mac(re, -vh[u].x, -vl[u].x, h.x, h.y);
+            df_mac(re, vh[u].y, vl[u].y, h.z, h.w);
+            df_mac(im, -vh[u].x, -vl[u].x, h.z, h.w);
+            df_mac(im, -vh[u].y, -vl[u].y, h.x, h.y);
+        }
+    }
+    for (; i < nvec; ++i) {
+        const float2 vh = V[(int64_t)i * vstride + e], vl = V[(int64_t)i * vstride + nm + e];
+        const float4 h = hdf[i * m + c];
+        df_mac(re, -vh.x, -vl.x, h.x, h.y);
+        df_mac(re, vh.y, vl.y, h.z, h.w);
+        df_mac(im, -vh.x, -vl.x, h.z, h.w);
+        df_mac(im, -vh.y, -vl.y, h.x, h.y);
+    }
+    re = df_norm(re);
+    im = df_norm(im);
+    W[e] = make_float2(re.h, im.h);
+    W[nm + e] = make_float2(re.l, im.l);
+}
+
+// V = W s per column (W, V double-float, s double-float [m])
+__global__ void scale_df_kernel(int64_t nm, int m, const float2* __restrict__ W, const float2* __restrict__ s,
+                                float2* __restrict__ V) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nm) return;
+    const float2 f = s[e % m];
+    const float2 wh = W[e], wl = W[nm + e];
+    const dfl re = df_mul(wh.x, wl.x, f.x, f.y), im = df_mul(wh.y, wl.y, f.x, f.y);
+    V[e] = make_float2(re.h, im.h);
+    V[nm + e] = make_float2(re.l, im.l);
+}
+
+// X += sum_i Z_i y_i per column (Z_i exact in FP32, X double-float, y
+// double-float [nvec][m])
+__global__ void __launch_bounds__(256) lincomb_df_kernel(int64_t nm, int m, int nvec, const float2* __restrict__ Z,
+                                                         int64_t zstride, const float4* __restrict__ ydf,
+                                                         float2* __restrict__ X) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nm) return;
+    const int c = (int)(e % m);
+    const float2 xh = X[e], xl = X[nm + e];
+    dfl re = {xh.x, xl.x}, im = {xh.y, xl.y};
+    for (int i = 0; i < nvec; ++i) {
+        const float2 z = Z[(int64_t)i * zstride + e];
+        const float4 y = ydf[i * m + c];
+        df_mac1(re, z.x, y.x, y.y);
+        df_mac1(re, -z.y, y.z, y.w);
+        df_mac1(im, z.x, y.z, y.w);
+        df_mac1(im, z.y, y.x, y.y);
+    }
+    re = df_norm(re);
+    im = df_norm(im);
+    X[e] = make_float2(re.h, im.h);
+    X[nm + e] = make_float2(re.l, im.l);
+}
+
+// double-float planes of a c128 array of count entries, and back
+__global__ void split_c128_kernel(int64_t count, const double2* __restrict__ a, float2* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const double2 v = a[e];
+    const float2 x = df_split(v.x), y = df_split(v.y);
+    out[e] = make_float2(x.x, y.x);
+    out[count + e] = make_float2(x.y, y.y);
+}
+
+__global__ void join_c128_kernel(int64_t count, const float2* __restrict__ in, double2* __restrict__ a) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const float2 h = in[e], l = in[count + e];
+    a[e] = make_double2(df_join(h.x, l.x), df_join(h.y, l.y));
+}
+
 // ----------------------------------------------------------------------------
 static inline unsigned nblocks(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
 
@@ -310,7 +471,6 @@ void Gmres<C>::reserve(int64_t n_, int m_, int restart_) {
     m = m_;
     restart = restart_;
     V.ensure((size_t)(restart + 1) * n * m);
-    reorth_passes = 0;
     Z.ensure((size_t)restart * n * m);
     W.ensure((size_t)n * m);
     H.ensure((size_t)restart * (restart + 1) * m);
@@ -325,15 +485,24 @@ void Gmres<C>::reserve(int64_t n_, int m_, int restart_) {
     ivec.ensure((size_t)4 * m + 4);
 }
 
+// out[i][c] = conj(V_i)^T w for i < nvec (+ conj(w)^T w at nvec when self = 1),
+// acc[i] += out[i] for i < nvec, hdf = out as double-floats (optional)
+template <typename C>
+static void dots_launch(int64_t n, int m, const C* Vb, int nvec, int64_t vstride, const C* w, double2* partial,
+                        double2* out, double2* acc, float4* hdf, cudaStream_t st, int self) {
+    dim3 blk(32, 8), grd(kDotBlocks, (m + 31) / 32);
+    dots_kernel<C><<<grd, blk, 0, st>>>(n, m, nvec, Vb, vstride, w, self, partial);
+    MWI_CHECK_LAUNCH();
+    const int nt = nvec + self;
+    dots_reduce_kernel<<<nblocks((int64_t)nt * m, 128), 128, 0, st>>>(kDotBlocks, nt, nvec, m, partial, out, acc,
+                                                                       hdf);
+    MWI_CHECK_LAUNCH();
+}
+
 template <typename C>
 void Gmres<C>::dots(const C* Vb, int nvec, int64_t vstride, const C* w, double2* out, double2* acc,
                     cudaStream_t st, int self) {
-    dim3 blk(32, 8), grd(kDotBlocks, (m + 31) / 32);
-    dots_kernel<C><<<grd, blk, 0, st>>>(n, m, nvec, Vb, vstride, w, self, partial.p);
-    MWI_CHECK_LAUNCH();
-    const int nt = nvec + self;
-    dots_reduce_kernel<<<nblocks((int64_t)nt * m, 128), 128, 0, st>>>(kDotBlocks, nt, nvec, m, partial.p, out, acc);
-    MWI_CHECK_LAUNCH();
+    dots_launch<C>(n, m, Vb, nvec, vstride, w, partial.p, out, acc, nullptr, st, self);
 }
 
 template <typename C>
@@ -361,9 +530,8 @@ int Gmres<C>::cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const doubl
     int* active = ivec.p;
     int* kcol = ivec.p + m;
     int* nact = ivec.p + 4 * m;
-    int* flag = ivec.p + 4 * m + 1;
     column_norms2(r0, beta2, st);
-    cycle_start_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, beta2, tol, active, kcol, g.p, inv, resid);
+    cycle_start_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, beta2, tol, active, kcol, g.p, inv, resid, nullptr);
     MWI_CHECK_LAUNCH();
     scale_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, r0, inv, V.p);
     MWI_CHECK_LAUNCH();
@@ -374,35 +542,21 @@ int Gmres<C>::cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const doubl
         C* zk = Z.p + (int64_t)k * vs;
         M(vk, zk);
         A(zk, W.p);
-        // classical Gram-Schmidt with selective reorthogonalisation: the second
-        // pass runs when some column lost more than half of its squared norm
-        // in the first (the usual twice-is-enough criterion)
+        // classical Gram-Schmidt applied twice (CGS2)
         auto ortho = [&] {
             MWI_CUDA(cudaMemsetAsync(hacc.p, 0, (size_t)(k + 1) * m * sizeof(double2), st));
-            dots(V.p, k + 1, vs, W.p, h.p, hacc.p, st, 1);
-            const double2* w0sq = h.p + (int64_t)(k + 1) * m;
-            cgs_update_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, k + 1, V.p, vs, h.p, W.p);
-            MWI_CHECK_LAUNCH();
-            column_norms2_into(W.p, hn2, h.p + (int64_t)(k + 2) * m, st);
-            MWI_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-            reorth_test_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, w0sq, hn2, flag);
-            MWI_CHECK_LAUNCH();
-            int again = 0;
-            MWI_CUDA(cudaMemcpyAsync(&again, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-            MWI_CUDA(cudaStreamSynchronize(st));
-            if (again) {
-                ++reorth_passes;
+            for (int pass = 0; pass < 2; ++pass) {
                 dots(V.p, k + 1, vs, W.p, h.p, hacc.p, st, 0);
                 cgs_update_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, k + 1, V.p, vs, h.p, W.p);
                 MWI_CHECK_LAUNCH();
-                column_norms2(W.p, hn2, st);
             }
+            column_norms2(W.p, hn2, st);
         };
         if (timer) timer(2, ortho);
         else ortho();
         MWI_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), st));
         arnoldi_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, k, restart, hacc.p, hn2, H.p, cs.p, sn.p, g.p, active,
-                                                        kcol, tol, resid, inv, nact);
+                                                        kcol, tol, resid, inv, nact, nullptr);
         MWI_CHECK_LAUNCH();
         if (k + 1 < max_steps) {
             scale_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, W.p, inv, V.p + (int64_t)(k + 1) * vs);
@@ -412,7 +566,7 @@ int Gmres<C>::cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const doubl
         MWI_CUDA(cudaStreamSynchronize(st));
         if (n_active_host == 0) { ++k; break; }
     }
-    lsq_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, restart, H.p, g.p, kcol, y.p);
+    lsq_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, restart, H.p, g.p, kcol, y.p, nullptr);
     MWI_CHECK_LAUNCH();
     lincomb_kernel<C><<<nblocks(nm, 256), 256, 0, st>>>(n, m, k, Z.p, vs, y.p, x);
     MWI_CHECK_LAUNCH();
@@ -426,6 +580,140 @@ int Gmres<C>::cycle(const OpFn& A, const OpFn& M, const C* r0, C* x, const doubl
 
 template struct Gmres<double2>;
 template struct Gmres<float2>;
+
+// ---------------------------------------------------------------- double-float FGMRES
+void GmresDF::reserve(int64_t n_, int m_, int restart_) {
+    n = n_;
+    m = m_;
+    restart = restart_;
+    V.ensure((size_t)(restart + 1) * 2 * n * m);
+    Z.ensure((size_t)restart * n * m);
+    W.ensure((size_t)2 * n * m);
+    H.ensure((size_t)restart * (restart + 1) * m);
+    cs.ensure((size_t)restart * m);
+    sn.ensure((size_t)restart * m);
+    g.ensure((size_t)(restart + 1) * m);
+    y.ensure((size_t)restart * m);
+    h.ensure((size_t)(restart + 2) * m);
+    hacc.ensure((size_t)(restart + 1) * m);
+    partial.ensure((size_t)kDotBlocks * (restart + 2) * m);
+    hdf.ensure((size_t)(restart + 1) * m);
+    ydf.ensure((size_t)restart * m);
+    invdf.ensure((size_t)m);
+    dvec.ensure((size_t)8 * m);
+    ivec.ensure((size_t)4 * m + 4);
+}
+
+void GmresDF::norms2(const float2* xh, double* out, cudaStream_t st) {
+    dots_launch<float2>(n, m, xh, 0, 0, xh, partial.p, h.p, nullptr, nullptr, st, 1);
+    real_part_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, h.p, out);
+    MWI_CHECK_LAUNCH();
+}
+
+int GmresDF::cycle(const OpA& A, const OpM& M, const float2* r0, float2* x, const double* tol, int max_steps,
+                   cudaStream_t st, int* iters_used) {
+    const int64_t nm = n * m;
+    const int64_t vs = 2 * nm;  // stride of the double-float basis vectors
+    double* beta2 = dvec.p;
+    double* inv = dvec.p + m;
+    double* resid = dvec.p + 2 * m;
+    double* hn2 = dvec.p + 3 * m;
+    int* active = ivec.p;
+    int* kcol = ivec.p + m;
+    int* nact = ivec.p + 4 * m;
+    norms2(r0, beta2, st);
+    cycle_start_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, beta2, tol, active, kcol, g.p, inv, resid, invdf.p);
+    MWI_CHECK_LAUNCH();
+    scale_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, r0, invdf.p, V.p);
+    MWI_CHECK_LAUNCH();
+    int k = 0;
+    int n_active_host = 1;
+    for (; k < max_steps; ++k) {
+        float2* vk = V.p + (int64_t)k * vs;
+        float2* zk = Z.p + (int64_t)k * nm;
+        // the preconditioner sees the FP32 head of v_k; z_k is stored exactly
+        M(vk, zk);
+        A(zk, W.p);
+        // CGS2: coefficients from the FP32 heads (their rounding only costs
+        // orthogonality at the 1e-7 level, which the second pass keeps from
+        // growing), updates in double-float so that A z_k = V h holds to
+        // double-float accuracy
+        auto ortho = [&] {
+            MWI_CUDA(cudaMemsetAsync(hacc.p, 0, (size_t)(k + 1) * m * sizeof(double2), st));
+            for (int pass = 0; pass < 2; ++pass) {
+                dots_launch<float2>(n, m, V.p, k + 1, vs, W.p, partial.p, h.p, hacc.p, hdf.p, st, 0);
+                cgs_update_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, k + 1, V.p, vs, hdf.p, W.p);
+                MWI_CHECK_LAUNCH();
+            }
+            norms2(W.p, hn2, st);
+        };
+        if (timer) timer(2, ortho);
+        else ortho();
+        MWI_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), st));
+        arnoldi_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, k, restart, hacc.p, hn2, H.p, cs.p, sn.p, g.p, active,
+                                                        kcol, tol, resid, inv, nact, invdf.p);
+        MWI_CHECK_LAUNCH();
+        if (k + 1 < max_steps) {
+            scale_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, W.p, invdf.p, V.p + (int64_t)(k + 1) * vs);
+            MWI_CHECK_LAUNCH();
+        }
+        MWI_CUDA(cudaMemcpyAsync(&n_active_host, nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+        if (n_active_host == 0) { ++k; break; }
+    }
+    lsq_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, restart, H.p, g.p, kcol, y.p, ydf.p);
+    MWI_CHECK_LAUNCH();
+    lincomb_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, k, Z.p, nm, ydf.p, x);
+    MWI_CHECK_LAUNCH();
+    if (iters_used) *iters_used = k;
+    return k;
+}
+
+void spmm_df(int64_t n, const int32_t* row_ptr, const int32_t* col, const float2* A, int64_t nnz, const float2* x,
+             float2* w, int m, cudaStream_t st) {
+    const int th = 256;
+    const int G = m >= 32 ? 32 : (m >= 8 ? 8 : 4);
+    const unsigned blocks = (unsigned)((n * G + th - 1) / th);
+    const int64_t nm = n * m;
+    if (G == 32)
+        spmm_df_kernel<32, false><<<blocks, th, 0, st>>>(n, row_ptr, col, A, A + nnz, x, nullptr, nullptr, nullptr, w,
+                                                         w + nm, m);
+    else if (G == 8)
+        spmm_df_kernel<8, false><<<blocks, th, 0, st>>>(n, row_ptr, col, A, A + nnz, x, nullptr, nullptr, nullptr, w,
+                                                        w + nm, m);
+    else
+        spmm_df_kernel<4, false><<<blocks, th, 0, st>>>(n, row_ptr, col, A, A + nnz, x, nullptr, nullptr, nullptr, w,
+                                                        w + nm, m);
+    MWI_CHECK_LAUNCH();
+}
+
+void residual_df(int64_t n, const int32_t* row_ptr, const int32_t* col, const float2* A, int64_t nnz, const float2* b,
+                 const float2* x, float2* r, int m, cudaStream_t st) {
+    const int th = 256;
+    const int G = m >= 32 ? 32 : (m >= 8 ? 8 : 4);
+    const unsigned blocks = (unsigned)((n * G + th - 1) / th);
+    const int64_t nm = n * m;
+    if (G == 32)
+        spmm_df_kernel<32, true><<<blocks, th, 0, st>>>(n, row_ptr, col, A, A + nnz, x, x + nm, b, b + nm, r, r + nm,
+                                                        m);
+    else if (G == 8)
+        spmm_df_kernel<8, true><<<blocks, th, 0, st>>>(n, row_ptr, col, A, A + nnz, x, x + nm, b, b + nm, r, r + nm,
+                                                       m);
+    else
+        spmm_df_kernel<4, true><<<blocks, th, 0, st>>>(n, row_ptr, col, A, A + nnz, x, x + nm, b, b + nm, r, r + nm,
+                                                       m);
+    MWI_CHECK_LAUNCH();
+}
+
+void split_c128(int64_t count, const double2* a, float2* out, cudaStream_t st) {
+    split_c128_kernel<<<nblocks(count, 256), 256, 0, st>>>(count, a, out);
+    MWI_CHECK_LAUNCH();
+}
+
+void join_c128(int64_t count, const float2* in, double2* a, cudaStream_t st) {
+    join_c128_kernel<<<nblocks(count, 256), 256, 0, st>>>(count, in, a);
+    MWI_CHECK_LAUNCH();
+}
 
 void convert_c128_to_c64(int64_t nm, const double2* a, float2* b, cudaStream_t st) {
     convert_kernel<double2, float2><<<nblocks(nm, 256), 256, 0, st>>>(nm, a, b);
