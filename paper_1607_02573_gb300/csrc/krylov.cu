@@ -125,26 +125,46 @@ __global__ void __launch_bounds__(256) dots_kernel(int64_t n, int m, int nvec_in
 }
 
 // h[i][c] = sum_b partial[b][i][c] for i < nvec; hacc[i][c] += h[i][c] for i < nacc;
-// hdf (optional) receives h as double-floats (re hi, re lo, im hi, im lo)
-__global__ void dots_reduce_kernel(int nblk, int nvec, int nacc, int m, const double2* __restrict__ partial,
-                                   double2* __restrict__ h, double2* __restrict__ hacc, float4* __restrict__ hdf) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nvec * m) return;
-    double2 s = make_double2(0.0, 0.0);
-    for (int b = 0; b < nblk; ++b) {
-        double2 v = partial[(int64_t)b * nvec * m + e];
-        s.x += v.x;
-        s.y += v.y;
-    }
-    h[e] = s;
-    if (hacc && e < nacc * m) { hacc[e].x += s.x; hacc[e].y += s.y; }
-    if (hdf) {
-        const float2 a = df_split(s.x), b = df_split(s.y);
-        hdf[e] = make_float4(a.x, a.y, b.x, b.y);
+// hdf (optional) receives h as double-floats (re hi, re lo, im hi, im lo).
+// One block per vector index i: 8 warps split the blocks b (b = lane, lane + 8,
+// ...), lanes over columns, then a fixed-order sum of the 8 partial sums.
+__global__ void __launch_bounds__(256) dots_reduce_kernel(int nblk, int nvec, int nacc, int m,
+                                                          const double2* __restrict__ partial,
+                                                          double2* __restrict__ h, double2* __restrict__ hacc,
+                                                          float4* __restrict__ hdf) {
+    __shared__ double2 red[8][32];
+    const int i = blockIdx.x;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < m; c0 += 32) {
+        const int c = c0 + tx;
+        double sx = 0.0, sy = 0.0;
+        if (c < m) {
+#pragma unroll 4
+            for (int b = ty; b < nblk; b += 8) {
+                const double2 v = partial[((int64_t)b * nvec + i) * m + c];
+                sx += v.x;
+                sy += v.y;
+            }
+        }
+        red[ty][tx] = make_double2(sx, sy);
+        __syncthreads();
+        if (ty == 0 && c < m) {
+            double2 s = red[0][tx];
+            for (int k = 1; k < 8; ++k) {
+                s.x += red[k][tx].x;
+                s.y += red[k][tx].y;
+            }
+            const int e = i * m + c;
+            h[e] = s;
+            if (hacc && i < nacc) { hacc[e].x += s.x; hacc[e].y += s.y; }
+            if (hdf) {
+                const float2 a = df_split(s.x), b = df_split(s.y);
+                hdf[e] = make_float4(a.x, a.y, b.x, b.y);
+            }
+        }
+        __syncthreads();
     }
 }
-
-
 
 // W[r][c] -= sum_i V_i[r][c] h[i][c]
 template <typename C>
@@ -494,8 +514,7 @@ static void dots_launch(int64_t n, int m, const C* Vb, int nvec, int64_t vstride
     dots_kernel<C><<<grd, blk, 0, st>>>(n, m, nvec, Vb, vstride, w, self, partial);
     MWI_CHECK_LAUNCH();
     const int nt = nvec + self;
-    dots_reduce_kernel<<<nblocks((int64_t)nt * m, 128), 128, 0, st>>>(kDotBlocks, nt, nvec, m, partial, out, acc,
-                                                                       hdf);
+    dots_reduce_kernel<<<nt, 256, 0, st>>>(kDotBlocks, nt, nvec, m, partial, out, acc, hdf);
     MWI_CHECK_LAUNCH();
 }
 
