@@ -271,6 +271,18 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     up(F.child_ptr, D.child_ptr, st); up(F.child, D.child, st);
     up(F.urows, D.urows, st); up(F.urel, D.urel, st);
     up(F.asm_base, D.asm_base, st); up(F.asm_ptr, D.asm_ptr, st); up(F.asm_src, D.asm_src, st);
+    {
+        // every front row receives at most one row from each of its (at most two) children
+        const int64_t rows = (int64_t)D.asm_ptr.size() - 1;
+        std::vector<int2> a2(std::max<int64_t>(1, rows), make_int2(-1, -1));
+        for (int64_t r = 0; r < rows; ++r) {
+            const int64_t q0 = D.asm_ptr[r], q1 = D.asm_ptr[r + 1];
+            MWI_REQUIRE(q1 - q0 <= 2, MWI_EINVAL, "internal: more than two extend-add sources for a front row");
+            if (q1 > q0) a2[r].x = D.asm_src[q0];
+            if (q1 > q0 + 1) a2[r].y = D.asm_src[q0 + 1];
+        }
+        up(F.asm2, a2, st);
+    }
     up(F.amap_front_ptr, D.amap_front_ptr, st); up(F.amap_slot, D.amap_slot, st); up(F.amap_pos, D.amap_pos, st);
     up(F.level_fronts, D.level_fronts, st);
     F.level_ptr = D.level_ptr;
@@ -279,7 +291,7 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     F.level_fmax.assign(nlev, 0);
     F.level_umax.assign(nlev, 0);
     F.level_pmean.assign(nlev, 0.0);
-    F.level_umean.assign(nlev, 0.0);
+    F.level_fmean.assign(nlev, 0.0);
     for (int l = 0; l < nlev; ++l)
         for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
             const Front& fr = D.fronts[D.level_fronts[q]];
@@ -287,12 +299,12 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
             F.level_fmax[l] = std::max(F.level_fmax[l], fr.p + fr.u);
             F.level_umax[l] = std::max(F.level_umax[l], fr.u);
             F.level_pmean[l] += fr.p;
-            F.level_umean[l] += fr.u;
+            F.level_fmean[l] += fr.p + fr.u;
         }
     for (int l = 0; l < nlev; ++l) {
         const double cnt = std::max(1, D.level_ptr[l + 1] - D.level_ptr[l]);
         F.level_pmean[l] /= cnt;
-        F.level_umean[l] /= cnt;
+        F.level_fmean[l] /= cnt;
     }
     up(F.sub_off, D.sub_off, st);
     up(F.loc2glob, D.loc2glob, st);
@@ -306,27 +318,37 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     F.sch_entries[0] = D.sch_entries[0];
     F.sch_entries[1] = D.sch_entries[1];
     F.n_sub = D.n_sub;
-    // GEMM tile lists of the sweeps and per-level offsets of the L11^-1 scratch
+    // GEMM tile lists of the sweeps and per-level offsets of the inverse scratch
     for (int pass = 0; pass < 2; ++pass) {
         TileLists& TL = pass == 0 ? F.tiles64 : F.tiles32;
         TL.tm = sweep_tile_rows(pass == 0);
-        std::vector<int2> pt, ut;
+        std::vector<TileDesc> pt, ft;
         TL.p_ptr.assign(1, 0);
-        TL.u_ptr.assign(1, 0);
+        TL.f_ptr.assign(1, 0);
         for (int l = 0; l < nlev; ++l) {
             for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
                 const int sid = D.level_fronts[q];
                 const Front& fr = D.fronts[sid];
-                for (int r = 0; r < fr.p; r += TL.tm) pt.push_back(make_int2(sid, r));
-                for (int r = 0; r < fr.u; r += TL.tm) ut.push_back(make_int2(sid, r));
+                TileDesc d;
+                d.a_off = fr.f_off;
+                d.sbase = D.sub_off[fr.sub];
+                d.rowbase = d.sbase + fr.start;
+                d.upd_row = fr.upd_row;
+                d.asm_base = D.asm_base[sid];
+                d.u_off = fr.u_off;
+                d.p = fr.p;
+                d.f = fr.p + fr.u;
+                d.pad = 0;
+                for (int r = 0; r < fr.p; r += TL.tm) { d.row0 = r; pt.push_back(d); }
+                for (int r = 0; r < fr.p + fr.u; r += TL.tm) { d.row0 = r; ft.push_back(d); }
             }
             TL.p_ptr.push_back((int64_t)pt.size());
-            TL.u_ptr.push_back((int64_t)ut.size());
+            TL.f_ptr.push_back((int64_t)ft.size());
         }
-        if (pt.empty()) pt.push_back(make_int2(0, 0));
-        if (ut.empty()) ut.push_back(make_int2(0, 0));
+        if (pt.empty()) pt.push_back(TileDesc{});
+        if (ft.empty()) ft.push_back(TileDesc{});
         TL.p_tiles.upload(pt, st);
-        TL.u_tiles.upload(ut, st);
+        TL.f_tiles.upload(ft, st);
     }
     {
         std::vector<int64_t> io(D.level_fronts.size());
@@ -335,8 +357,8 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
             int64_t acc = 0;
             for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
                 io[q] = acc;
-                const int64_t pp = D.fronts[D.level_fronts[q]].p;
-                acc += pp * pp;
+                const Front& fr = D.fronts[D.level_fronts[q]];
+                acc += (int64_t)fr.p * (fr.p + fr.u);
             }
             F.inv_entries = std::max(F.inv_entries, acc);
         }
@@ -374,7 +396,7 @@ void numeric_setup(mwi_problem* P) {
     P->perturbed.ensure(1);
     MWI_CUDA(cudaMemsetAsync(P->perturbed.p, 0, sizeof(int), st));
     if (mixed) {
-        P->ws32.ensure(E.F.ws_entries);
+        P->ws32.ensure(E.F.ws_total());
         P->inv32.ensure(std::max<int64_t>(1, E.F.inv_entries));
         for (int k = 0; k < 2; ++k) P->sch32[k].ensure(std::max<int64_t>(1, E.F.sch_entries[k]));
         float2* sch[2] = {P->sch32[0].p, P->sch32[1].p};
@@ -382,7 +404,7 @@ void numeric_setup(mwi_problem* P) {
             factorize_fronts<float2>(E.F, P->Bval.p, P->ws32.p, sch, P->inv32.p, P->perturbed.p, st);
         });
     } else {
-        P->ws64.ensure(E.F.ws_entries);
+        P->ws64.ensure(E.F.ws_total());
         P->inv64.ensure(std::max<int64_t>(1, E.F.inv_entries));
         for (int k = 0; k < 2; ++k) P->sch64[k].ensure(std::max<int64_t>(1, E.F.sch_entries[k]));
         double2* sch[2] = {P->sch64[0].p, P->sch64[1].p};

@@ -17,9 +17,11 @@
 // with unit diagonal implied, D on the diagonal), and its u x u Schur block in
 // a transient buffer shared by the fronts of one level (two buffers, even and
 // odd levels, since a level's blocks are consumed by the next level).  Once a
-// level is factorised, the p x p unit-lower block L11 of each of its fronts is
-// replaced by its inverse (partitioned inverse), so that the ORAS sweeps
-// become dependency-free dense products (sweep.cu).
+// level is factorised, each panel [L11; L21] is replaced by the first p
+// columns of the inverse of [L11 0; L21 I], i.e. [L11^{-1}; -L21 L11^{-1}]
+// (partitioned inverse) with a unit diagonal, and D^{-1} is stored after the
+// panels (indexed by local row), so that each front's part of the ORAS sweeps
+// is one dependency-free dense product per direction (sweep.cu).
 #include <algorithm>
 
 #include "common.h"
@@ -215,16 +217,20 @@ __global__ void __launch_bounds__(256) update_kernel(const int32_t* __restrict__
     }
 }
 
-// L11^{-1} for every front of a level (partitioned inverse used by the
-// sweeps): block (front, RC columns c0..) solves L11 X = I[:, c0:c0+RC] for
-// rows >= c0 by column-blocked forward substitution (warp-synchronous
-// triangles, row updates below), writing the strictly lower part of X to tmp.
+// Partitioned inverse of every front of a level, used by the sweeps.  The
+// panel [L11; L21] is the first p columns of the unit lower triangular
+// [L11 0; L21 I], whose inverse has first p columns [L11^{-1}; -L21 L11^{-1}].
+// Block (front, RC columns c0..) computes those columns for rows >= c0 by
+// column-blocked forward substitution (warp-synchronous 32 x 32 triangles on
+// the pivot rows, row updates below them, the update rows included), writing
+// the strictly lower part to tmp (per front f x p, ld f).
 template <typename C, int RC>
-__global__ void __launch_bounds__(256) invert_l11_kernel(const int32_t* __restrict__ level_fronts, int lo,
-                                                         const int32_t* __restrict__ P, const int32_t* __restrict__ U,
-                                                         const int64_t* __restrict__ f_off,
-                                                         const int64_t* __restrict__ inv_off,
-                                                         const C* __restrict__ ws, C* __restrict__ tmp) {
+__global__ void __launch_bounds__(256) invert_panel_kernel(const int32_t* __restrict__ level_fronts, int lo,
+                                                           const int32_t* __restrict__ P,
+                                                           const int32_t* __restrict__ U,
+                                                           const int64_t* __restrict__ f_off,
+                                                           const int64_t* __restrict__ inv_off,
+                                                           const C* __restrict__ ws, C* __restrict__ tmp) {
     constexpr int RP = RC + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* w = reinterpret_cast<C*>(smem_raw);
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(256) invert_l11_kernel(const int32_t* __restri
     const int64_t f = (int64_t)p + U[s];
     const C* L = ws + f_off[s];
     C* T = tmp + inv_off[lo + blockIdx.y];
-    const int nr = p - c0;
+    const int nr = (int)f - c0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < nr * RC; e += 256) {
         const int i = e / RC, r = e - i * RC;
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(256) invert_l11_kernel(const int32_t* __restri
             if (lane < nb) w[(jb - c0 + lane) * RP + warp] = val;
         }
         __syncthreads();
-        for (int i = jb + nb + tid; i < p; i += 256) {
+        for (int i = jb + nb + tid; i < (int)f; i += 256) {
             C acc[RC];
 #pragma unroll
             for (int r = 0; r < RC; ++r) acc[r] = w[(i - c0) * RP + r];
@@ -278,22 +284,31 @@ __global__ void __launch_bounds__(256) invert_l11_kernel(const int32_t* __restri
     __syncthreads();
     for (int e = tid; e < nr * RC; e += 256) {
         const int i = e / RC, r = e - i * RC;
-        if (c0 + r < p && i > r) T[(int64_t)(c0 + r) * p + c0 + i] = w[i * RP + r];
+        if (c0 + r < p && i > r) T[(int64_t)(c0 + r) * f + c0 + i] = w[i * RP + r];
     }
 }
 
+// panel column j <- [L11^{-1}; -L21 L11^{-1}] with a unit diagonal and zeros
+// above it (so that the panel is the sweeps' operand as stored), and
+// 1 / D_jj into dinv at the pivot's local row
 template <typename C>
-__global__ void copy_linv_kernel(const int32_t* __restrict__ level_fronts, int lo, const int32_t* __restrict__ P,
-                                 const int32_t* __restrict__ U, const int64_t* __restrict__ f_off,
-                                 const int64_t* __restrict__ inv_off, const C* __restrict__ tmp, C* __restrict__ ws) {
+__global__ void copy_inverse_kernel(const int32_t* __restrict__ level_fronts, int lo, const int32_t* __restrict__ P,
+                                    const int32_t* __restrict__ U, const int32_t* __restrict__ start,
+                                    const int32_t* __restrict__ sub, const int64_t* __restrict__ sub_off,
+                                    const int64_t* __restrict__ f_off, const int64_t* __restrict__ inv_off,
+                                    const C* __restrict__ tmp, C* __restrict__ ws, C* __restrict__ dinv) {
     const int s = level_fronts[lo + blockIdx.y];
     const int p = P[s];
     const int j = blockIdx.x;
     if (j >= p) return;
     const int64_t f = (int64_t)p + U[s];
-    C* L = ws + f_off[s];
-    const C* T = tmp + inv_off[lo + blockIdx.y];
-    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) L[(int64_t)j * f + i] = T[(int64_t)j * p + i];
+    C* L = ws + f_off[s] + (int64_t)j * f;
+    const C* T = tmp + inv_off[lo + blockIdx.y] + (int64_t)j * f;
+    const C d = L[j];
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < f; i += blockDim.x)
+        L[i] = i > j ? T[i] : (i == j ? cmake<C>(1, 0) : czero<C>());
+    if (threadIdx.x == 0) dinv[sub_off[sub[s]] + start[s] + j] = crecip(d);
 }
 
 template <typename C> struct FactorCfg;
@@ -301,30 +316,47 @@ template <> struct FactorCfg<float2> { static constexpr int NB = 32; static cons
 template <> struct FactorCfg<double2> { static constexpr int NB = 16; static constexpr int TILE = 32; };
 
 template <typename C, int RC>
-static void invert_level(const FrontsDev& F, int l, int lo, int nf, C* ws, C* tmp, cudaStream_t st) {
+static void invert_level_rc(const FrontsDev& F, int l, int lo, int nf, C* ws, C* tmp, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        MWI_CUDA(cudaFuncSetAttribute(invert_l11_kernel<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MWI_CUDA(cudaFuncSetAttribute(invert_panel_kernel<C, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       200 * 1024));
         attr = true;
     }
     const int pmax = F.level_pmax[l];
-    const size_t sm = (size_t)pmax * (RC + 1) * sizeof(C);
-    MWI_REQUIRE(sm <= 200 * 1024, MWI_EINVAL, "front too large for the shared-memory inversion");
+    const size_t sm = (size_t)F.level_fmax[l] * (RC + 1) * sizeof(C);
     dim3 grd((pmax + RC - 1) / RC, nf);
-    invert_l11_kernel<C, RC><<<grd, 256, sm, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.f_off.p, F.inv_off.p, ws,
-                                                   tmp);
+    invert_panel_kernel<C, RC><<<grd, 256, sm, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.f_off.p, F.inv_off.p, ws,
+                                                     tmp);
     MWI_CHECK_LAUNCH();
-    copy_linv_kernel<C><<<dim3(pmax, nf), 128, 0, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.f_off.p, F.inv_off.p,
-                                                        tmp, ws);
+    copy_inverse_kernel<C><<<dim3(pmax, nf), 128, 0, st>>>(F.level_fronts.p, lo, F.p.p, F.u.p, F.start.p, F.sub.p,
+                                                           F.sub_off.p, F.f_off.p, F.inv_off.p, tmp, ws,
+                                                           ws + F.ws_entries);
     MWI_CHECK_LAUNCH();
+}
+
+// widest column block whose substitution rows fit in 200 KB of shared memory
+template <typename C>
+static void invert_level(const FrontsDev& F, int l, int lo, int nf, C* ws, C* tmp, cudaStream_t st) {
+    const size_t row = (size_t)F.level_fmax[l] * sizeof(C);
+    const size_t lim = 200 * 1024;
+    if constexpr (sizeof(C) == sizeof(float2)) {
+        if (row * 9 <= lim) {
+            invert_level_rc<C, 8>(F, l, lo, nf, ws, tmp, st);
+            return;
+        }
+    }
+    if (row * 5 <= lim) invert_level_rc<C, 4>(F, l, lo, nf, ws, tmp, st);
+    else if (row * 3 <= lim) invert_level_rc<C, 2>(F, l, lo, nf, ws, tmp, st);
+    else if (row * 2 <= lim) invert_level_rc<C, 1>(F, l, lo, nf, ws, tmp, st);
+    else throw Error(MWI_EINVAL, "front too large for the shared-memory inversion");
 }
 
 template <typename C>
 void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const sch[2], C* inv_tmp, int* perturbed,
                       cudaStream_t st) {
     constexpr int NB = FactorCfg<C>::NB, TILE = FactorCfg<C>::TILE;
-    MWI_CUDA(cudaMemsetAsync(ws, 0, (size_t)F.ws_entries * sizeof(C), st));
+    MWI_CUDA(cudaMemsetAsync(ws, 0, (size_t)(F.ws_entries + F.nloc) * sizeof(C), st));
     const int nlev = (int)F.level_ptr.size() - 1;
     for (int l = 0; l < nlev; ++l) {
         const int lo0 = F.level_ptr[l], hi = F.level_ptr[l + 1];
@@ -361,8 +393,7 @@ void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const 
                                                                            F.f_off.p, F.sch_off.p, ws, sch_l);
                 MWI_CHECK_LAUNCH();
             }
-            if (sizeof(C) == sizeof(float2)) invert_level<C, 8>(F, l, lo, nf, ws, inv_tmp, st);
-            else invert_level<C, 4>(F, l, lo, nf, ws, inv_tmp, st);
+            invert_level<C>(F, l, lo, nf, ws, inv_tmp, st);
         }
     }
 }

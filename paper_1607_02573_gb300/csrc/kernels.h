@@ -56,12 +56,23 @@ void launch_slot_fill(const SlotMatrixDev& S, const double* K, const double* M, 
                       double2* out64, float2* out32, cudaStream_t st);
 
 // ---- multifrontal factorisation and ORAS application (factor.cu, sweep.cu, oras.cu)
-// GEMM tiles of the sweeps: (front, first row) per level, for pivot-row tiles
-// (FWD_P, BWD_T, BWD_X) and update-row tiles (FWD_U).
+// One GEMM tile of the sweeps: the front's geometry and the tile's first row.
+struct __align__(16) TileDesc {
+    int64_t a_off;     // panel offset in the factor store
+    int64_t rowbase;   // local row of the front's first pivot
+    int64_t sbase;     // local row of the subdomain's first row
+    int64_t upd_row;   // first row of the front's update vector
+    int64_t asm_base;  // first gather-table row of the front
+    int64_t u_off;     // first entry of the front's update-row list
+    int32_t p, f, row0, pad;
+};
+
+// GEMM tiles of the sweeps per level, over the p pivot rows (backward product,
+// extend-add) and over all f = p + u front rows (forward product).
 struct TileLists {
     int tm = 0;
-    DevBuf<int2> p_tiles, u_tiles;
-    std::vector<int64_t> p_ptr, u_ptr;  // [n_levels+1]
+    DevBuf<TileDesc> p_tiles, f_tiles;
+    std::vector<int64_t> p_ptr, f_ptr;  // [n_levels+1]
 };
 
 struct FrontsDev {
@@ -72,6 +83,7 @@ struct FrontsDev {
     DevBuf<int32_t> urows, urel;
     DevBuf<int64_t> asm_base, asm_ptr;   // gather lists of the sweeps' extend-add
     DevBuf<int32_t> asm_src;
+    DevBuf<int2> asm2;                   // the same lists as (source, source) per front row, -1 = none
     DevBuf<int64_t> amap_front_ptr, amap_slot, amap_pos;
     DevBuf<int32_t> level_fronts;
     std::vector<int32_t> level_ptr;   // host copy
@@ -83,14 +95,16 @@ struct FrontsDev {
     DevBuf<int64_t> own_ptr;
     DevBuf<int32_t> own_row;
     DevBuf<double> own_w;
+    // factor store: ws_entries panel entries, then D^{-1} for the nloc local rows
     int64_t nloc = 0, upd_rows = 0, ws_entries = 0;
+    int64_t ws_total() const { return ws_entries + nloc; }
     std::vector<int64_t> level_sch;    // host: sum u^2 of each level
     int64_t sch_entries[2] = {0, 0};
     int n_sub = 0;
     TileLists tiles64, tiles32;        // 64-row and 32-row tiles of every level
-    std::vector<double> level_pmean, level_umean;  // host: mean p and u of each level
-    DevBuf<int64_t> inv_off;           // per level position: offset of the front's p x p block
-    int64_t inv_entries = 0;           // largest sum of p^2 over a level
+    std::vector<double> level_pmean, level_fmean;  // host: mean p and f of each level
+    DevBuf<int64_t> inv_off;           // per level position: offset of the front's f x p block
+    int64_t inv_entries = 0;           // largest sum of f p over a level
 };
 
 // ws: factor store (panels); sch[2]: transient Schur buffers (even / odd levels)
