@@ -291,9 +291,18 @@ __global__ void __launch_bounds__(256, 4) sweep_mma_kernel(const TileDesc* __res
     }
     if (MODE == kBwd && ur_smem) __syncthreads();
 
+    // FWD: a warp takes 8 consecutive rows of 4 panel columns (full 32-byte
+    // sectors, 2-way bank conflicts on the stores); BWD: k fastest
     auto a_index = [&](int e, int& i, int& kk) {
-        if (MODE == kFwd) { i = e % TM; kk = e / TM; }
-        else { kk = e % KB; i = e / KB; }
+        if (MODE == kFwd) {
+            const int lane_ = e & 31, w = e >> 5;
+            constexpr int IG = TM / 8;
+            i = 8 * (w % IG) + (lane_ & 7);
+            kk = 4 * (w / IG) + (lane_ >> 3);
+        } else {
+            kk = e % KB;
+            i = e / KB;
+        }
     };
     auto loadA = [&](int kb, C* areg) {
 #pragma unroll
