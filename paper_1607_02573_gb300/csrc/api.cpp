@@ -31,7 +31,42 @@ struct DecompEntry {
     FrontsDev F;
     SlotMatrixDev B;
     DevBuf<int32_t> fu_face, fu_tet;
+    UpdateTiles ut[2];               // trailing-update tiles: [0] complex FP32, [1] complex FP64
+    std::once_flag ut_once[2];
 };
+
+// The factorisation's trailing-update tiles, in its consumption order: per
+// level, per chunk of at most 65535 fronts, per step k of nb pivot columns,
+// the lower-triangle tiles of every front of the chunk with k < p.
+void build_update_tiles(const Decomposition& D, int nb, int tile, UpdateTiles& ut, cudaStream_t st) {
+    std::vector<int4> t;
+    ut.nb = nb;
+    ut.tile = tile;
+    ut.ptr.assign(1, 0);
+    for (int l = 0; l < D.n_levels; ++l) {
+        const int lo0 = D.level_ptr[l], hi = D.level_ptr[l + 1];
+        int pmax = 0;
+        for (int q = lo0; q < hi; ++q) pmax = std::max(pmax, D.fronts[D.level_fronts[q]].p);
+        for (int lo = lo0; lo < hi; lo += 65535) {
+            const int nf = std::min(65535, hi - lo);
+            for (int k = 0; k < pmax; k += nb) {
+                for (int q = lo; q < lo + nf; ++q) {
+                    const int s = D.level_fronts[q];
+                    const Front& fr = D.fronts[s];
+                    if (k >= fr.p) continue;
+                    const int64_t nrem = (int64_t)fr.p + fr.u - k - std::min(nb, fr.p - k);
+                    const int T = (int)((nrem + tile - 1) / tile);
+                    for (int bi = 0; bi < T; ++bi)
+                        for (int bj = 0; bj <= bi; ++bj) t.push_back(make_int4(s, bi, bj, 0));
+                }
+                ut.ptr.push_back((int64_t)t.size());
+            }
+        }
+    }
+    if (t.empty()) t.push_back(make_int4(0, 0, 0, 0));
+    ut.tiles.upload(t, st);
+    MWI_CUDA(cudaStreamSynchronize(st));
+}
 
 template <typename T>
 static void up(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t st) { d.upload(h, st); }
@@ -283,6 +318,25 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
         }
         up(F.asm2, a2, st);
     }
+    {
+        std::vector<int4> et;
+        F.ext_ptr.assign(1, 0);
+        for (int l = 0; l < D.n_levels; ++l)
+            for (int lo = D.level_ptr[l]; lo < D.level_ptr[l + 1]; lo += 65535) {
+                const int nf = std::min(65535, D.level_ptr[l + 1] - lo);
+                for (int ci = 0; ci < 2; ++ci) {
+                    for (int q = lo; q < lo + nf; ++q) {
+                        const int sid = D.level_fronts[q];
+                        if (D.child_ptr[sid] + ci >= D.child_ptr[sid + 1]) continue;
+                        const int c = D.child[D.child_ptr[sid] + ci];
+                        for (int b = 0; b < D.fronts[c].u; b += 4) et.push_back(make_int4(sid, c, b, 0));
+                    }
+                    F.ext_ptr.push_back((int64_t)et.size());
+                }
+            }
+        if (et.empty()) et.push_back(make_int4(0, 0, 0, 0));
+        up(F.ext_tiles, et, st);
+    }
     up(F.amap_front_ptr, D.amap_front_ptr, st); up(F.amap_slot, D.amap_slot, st); up(F.amap_pos, D.amap_pos, st);
     up(F.level_fronts, D.level_fronts, st);
     F.level_ptr = D.level_ptr;
@@ -400,16 +454,22 @@ void numeric_setup(mwi_problem* P) {
         P->inv32.ensure(std::max<int64_t>(1, E.F.inv_entries));
         for (int k = 0; k < 2; ++k) P->sch32[k].ensure(std::max<int64_t>(1, E.F.sch_entries[k]));
         float2* sch[2] = {P->sch32[0].p, P->sch32[1].p};
+        std::call_once(E.ut_once[0], [&] {
+            build_update_tiles(E.D, factor_block_cols(true), factor_tile_rows(true), E.ut[0], st);
+        });
         timed(P, 3, [&] {
-            factorize_fronts<float2>(E.F, P->Bval.p, P->ws32.p, sch, P->inv32.p, P->perturbed.p, st);
+            factorize_fronts<float2>(E.F, E.ut[0], P->Bval.p, P->ws32.p, sch, P->inv32.p, P->perturbed.p, st);
         });
     } else {
         P->ws64.ensure(E.F.ws_total());
         P->inv64.ensure(std::max<int64_t>(1, E.F.inv_entries));
         for (int k = 0; k < 2; ++k) P->sch64[k].ensure(std::max<int64_t>(1, E.F.sch_entries[k]));
         double2* sch[2] = {P->sch64[0].p, P->sch64[1].p};
+        std::call_once(E.ut_once[1], [&] {
+            build_update_tiles(E.D, factor_block_cols(false), factor_tile_rows(false), E.ut[1], st);
+        });
         timed(P, 3, [&] {
-            factorize_fronts<double2>(E.F, P->Bval.p, P->ws64.p, sch, P->inv64.p, P->perturbed.p, st);
+            factorize_fronts<double2>(E.F, E.ut[1], P->Bval.p, P->ws64.p, sch, P->inv64.p, P->perturbed.p, st);
         });
     }
     MWI_CUDA(cudaMemcpyAsync(&P->n_perturbed, P->perturbed.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -43,21 +43,21 @@ __global__ void front_assemble_kernel(const int32_t* __restrict__ level_fronts, 
         ws[amap_pos[q]] = from_d2<C>(B[amap_slot[q]]);
 }
 
-// child ci of every front of the level: parent[urel[a], urel[b]] += S_c[a, b], a >= b,
-// where S_c is the child's Schur block and the parent entry lies in its panel
-// (pivot column) or in its own Schur block.
+// One block per (front, child, four child rows) tile: parent[urel[a], urel[b]]
+// += S_c[a, b], a >= b, where S_c is the child's Schur block and the parent
+// entry lies in its panel (pivot column) or in its own Schur block.  The first
+// and second children of the fronts go in separate launches (they add into the
+// same parent entries; the order is fixed, so no atomics are needed).
 template <typename C>
-__global__ void extend_add_kernel(const int32_t* __restrict__ level_fronts, int lo, int ci,
-                                  const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child,
-                                  const int32_t* __restrict__ P, const int32_t* __restrict__ U,
-                                  const int64_t* __restrict__ f_off, const int64_t* __restrict__ sch_off,
-                                  const int64_t* __restrict__ u_off, const int32_t* __restrict__ urel,
-                                  C* __restrict__ ws, const C* __restrict__ sch_child, C* __restrict__ sch_par) {
-    const int s = level_fronts[lo + blockIdx.y];
-    if (child_ptr[s] + ci >= child_ptr[s + 1]) return;
-    const int c = child[child_ptr[s] + ci];
+__global__ void extend_add_kernel(const int4* __restrict__ tiles, const int32_t* __restrict__ P,
+                                  const int32_t* __restrict__ U, const int64_t* __restrict__ f_off,
+                                  const int64_t* __restrict__ sch_off, const int64_t* __restrict__ u_off,
+                                  const int32_t* __restrict__ urel, C* __restrict__ ws, const C* __restrict__ sch_child,
+                                  C* __restrict__ sch_par) {
+    const int4 tl = tiles[blockIdx.x];  // (front, child, first child row)
+    const int s = tl.x, c = tl.y;
     const int uc = U[c];
-    const int b = blockIdx.x * blockDim.y + threadIdx.y;
+    const int b = tl.z + threadIdx.y;
     if (b >= uc) return;
     const int ps = P[s], us = U[s];
     const int64_t fs = (int64_t)ps + us;
@@ -80,9 +80,11 @@ __device__ __forceinline__ bool bad_pivot(C d) {
 }
 
 // Panel k..k+nb of every front of the level: factor the diagonal block in
-// shared memory, then L_i = x_i L11^{-T} D^{-1} for every row below.
+// shared memory (L unit lower, D on the diagonal), form M = L^{-T} D^{-1}
+// there, then every row below is L_i = a_i M (a_i = that row of the block
+// column): a small dense product, eight output columns at a time.
 template <typename C, int NB>
-__global__ void __launch_bounds__(256) panel_kernel(const int32_t* __restrict__ level_fronts, int lo, int k,
+__global__ void __launch_bounds__(128) panel_kernel(const int32_t* __restrict__ level_fronts, int lo, int k,
                                                     const int32_t* __restrict__ P, const int32_t* __restrict__ U,
                                                     const int64_t* __restrict__ f_off, C* __restrict__ ws,
                                                     int* __restrict__ perturbed) {
@@ -93,49 +95,80 @@ __global__ void __launch_bounds__(256) panel_kernel(const int32_t* __restrict__ 
     const int nb = min(NB, p - k);
     C* F = ws + f_off[s];
     __shared__ C Dg[NB][NB + 1];
+    __shared__ C M[NB][NB + 1];
     const int tid = threadIdx.x;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         int r = e % NB, c = e / NB;
         Dg[r][c] = (r < nb && c < nb && r >= c) ? F[(int64_t)(k + c) * f + k + r] : czero<C>();
     }
     __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-        C d = Dg[j][j];
-        if (bad_pivot(d)) {
-            __syncthreads();
-            if (tid == 0) {
-                Dg[j][j] = cmake<C>(1, 0);
-                atomicAdd(perturbed, 1);
+    // the diagonal block, by the first warp alone (lane r owns row r)
+    if (tid < 32) {
+        const int r = tid;
+        for (int j = 0; j < nb; ++j) {
+            C d = Dg[j][j];
+            if (bad_pivot(d)) {  // the same value in every lane
+                __syncwarp();
+                if (r == 0) {
+                    Dg[j][j] = cmake<C>(1, 0);
+                    atomicAdd(perturbed, 1);
+                }
+                d = cmake<C>(1, 0);
             }
-            __syncthreads();
-            d = Dg[j][j];
+            const bool below = r > j && r < nb;
+            C ld = czero<C>();
+            if (below) {
+                const C l = cmul(Dg[r][j], crecip(d));  // l_rj = a_rj / d_j
+                Dg[r][j] = l;
+                ld = cmul(l, d);
+            }
+            __syncwarp();
+            if (below)
+                for (int c = j + 1; c <= r; ++c) Dg[r][c] = csub(Dg[r][c], cmul(ld, Dg[c][j]));
+            __syncwarp();
         }
-        C dinv = crecip(d);
-        // l_rj = a_rj / d_j for r > j (each thread one r)
-        if (tid > j && tid < nb) Dg[tid][j] = cmul(Dg[tid][j], dinv);
-        __syncthreads();
-        for (int e = tid; e < nb * nb; e += blockDim.x) {
-            int r = e % nb, c = e / nb;
-            if (c > j && r >= c) Dg[r][c] = csub(Dg[r][c], cmul(cmul(Dg[r][j], d), Dg[c][j]));
-        }
-        __syncthreads();
     }
-    // rows below the diagonal block
+    __syncthreads();
+    // column j of M: y = L^{-T} e_j by back substitution, scaled by 1 / d_j
+    // (zero below the diagonal and outside the nb x nb block)
+    if (tid < NB) {
+        const int j = tid;
+        for (int r = NB - 1; r >= 0; --r) {
+            C y = czero<C>();
+            if (j < nb && r <= j) {
+                if (r == j) {
+                    y = cmake<C>(1, 0);
+                } else {
+                    for (int c = r + 1; c <= j; ++c) y = cfms(Dg[c][r], M[c][j], y);
+                }
+            }
+            M[r][j] = y;
+        }
+        if (j < nb) {
+            const C dj = crecip(Dg[j][j]);
+            for (int r = 0; r <= j; ++r) M[r][j] = cmul(M[r][j], dj);
+        }
+    }
+    __syncthreads();
+    // rows below the diagonal block: L_i = a_i M (M upper triangular): the
+    // row's output accumulates in registers while its entries stream in,
+    // eight independent loads at a time
     for (int64_t i = k + nb + tid; i < f; i += blockDim.x) {
-        C w[NB];
+        C acc[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) w[j] = j < nb ? F[(int64_t)(k + j) * f + i] : czero<C>();
+        for (int j = 0; j < NB; ++j) acc[j] = czero<C>();
+        for (int c0 = 0; c0 < nb; c0 += 8) {
+            C a[8];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            if (j >= nb) break;
-            C acc = w[j];
+            for (int q = 0; q < 8; ++q) a[q] = c0 + q < nb ? F[(int64_t)(k + c0 + q) * f + i] : czero<C>();
 #pragma unroll
-            for (int c = 0; c < j; ++c) acc = cfms(w[c], Dg[j][c], acc);
-            w[j] = acc;  // = (L_i D)_j
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int j = 0; j < NB; ++j) acc[j] = cfma(a[q], M[min(c0 + q, NB - 1)][j], acc[j]);
         }
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-            if (j < nb) F[(int64_t)(k + j) * f + i] = cmul(w[j], crecip(Dg[j][j]));
+            if (j < nb) F[(int64_t)(k + j) * f + i] = acc[j];
     }
     __syncthreads();
     for (int e = tid; e < nb * nb; e += blockDim.x) {
@@ -146,15 +179,15 @@ __global__ void __launch_bounds__(256) panel_kernel(const int32_t* __restrict__ 
 
 // Trailing update of the lower triangle: F[i][c] -= sum_j L[i][j] d_j L[c][j],
 // rows/cols in [k + nb, f).  TILE x TILE output tile per block, 256 threads.
+// One block per tile (front, bi, bj >= ... bi) of the level's tile list for step k.
 template <typename C, int TILE, int NB>
-__global__ void __launch_bounds__(256) update_kernel(const int32_t* __restrict__ level_fronts, int lo, int k,
+__global__ void __launch_bounds__(256) update_kernel(const int4* __restrict__ tiles, int k,
                                                      const int32_t* __restrict__ P, const int32_t* __restrict__ U,
                                                      const int64_t* __restrict__ f_off,
                                                      const int64_t* __restrict__ sch_off, C* __restrict__ ws,
                                                      C* __restrict__ sch) {
-    const int bi = blockIdx.y, bj = blockIdx.x;
-    if (bj > bi) return;
-    const int s = level_fronts[lo + blockIdx.z];
+    const int4 tl = tiles[blockIdx.x];
+    const int s = tl.x, bi = tl.y, bj = tl.z;
     const int p = P[s];
     if (k >= p) return;
     const int64_t f = (int64_t)p + U[s];
@@ -256,26 +289,32 @@ __global__ void __launch_bounds__(256) invert_panel_kernel(const int32_t* __rest
             Ld[i][j] = (i < nb && j < i) ? L[(int64_t)(jb + j) * f + jb + i] : czero<C>();
         }
         __syncthreads();
-        if (warp < RC) {
-            C val = lane < nb ? w[(jb - c0 + lane) * RP + warp] : czero<C>();
+        for (int r = warp; r < RC; r += 8) {
+            C val = lane < nb ? w[(jb - c0 + lane) * RP + r] : czero<C>();
             for (int j = 0; j < nb; ++j) {
                 C x;
                 x.x = __shfl_sync(0xffffffffu, val.x, j);
                 x.y = __shfl_sync(0xffffffffu, val.y, j);
                 val = cfms(Ld[lane][j], x, val);
             }
-            if (lane < nb) w[(jb - c0 + lane) * RP + warp] = val;
+            if (lane < nb) w[(jb - c0 + lane) * RP + r] = val;
         }
         __syncthreads();
         for (int i = jb + nb + tid; i < (int)f; i += 256) {
             C acc[RC];
 #pragma unroll
             for (int r = 0; r < RC; ++r) acc[r] = w[(i - c0) * RP + r];
-            for (int j = 0; j < nb; ++j) {
-                const C l = L[(int64_t)(jb + j) * f + i];
-                const C* wj = w + (jb + j - c0) * RP;
+            // eight panel entries of the row in flight at a time
+            for (int j0 = 0; j0 < nb; j0 += 8) {
+                C l[8];
 #pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = cfms(l, wj[r], acc[r]);
+                for (int q = 0; q < 8; ++q) l[q] = j0 + q < nb ? L[(int64_t)(jb + j0 + q) * f + i] : czero<C>();
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const C* wj = w + (jb + min(j0 + q, nb - 1) - c0) * RP;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) acc[r] = cfms(l[q], wj[r], acc[r]);
+                }
             }
 #pragma unroll
             for (int r = 0; r < RC; ++r) w[(i - c0) * RP + r] = acc[r];
@@ -353,11 +392,13 @@ static void invert_level(const FrontsDev& F, int l, int lo, int nf, C* ws, C* tm
 }
 
 template <typename C>
-void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const sch[2], C* inv_tmp, int* perturbed,
-                      cudaStream_t st) {
+void factorize_fronts(const FrontsDev& F, const UpdateTiles& ut, const double2* Bvals, C* ws, C* const sch[2],
+                      C* inv_tmp, int* perturbed, cudaStream_t st) {
     constexpr int NB = FactorCfg<C>::NB, TILE = FactorCfg<C>::TILE;
+    MWI_REQUIRE(ut.nb == NB && ut.tile == TILE, MWI_EINVAL, "internal: update tiles built for another blocking");
     MWI_CUDA(cudaMemsetAsync(ws, 0, (size_t)(F.ws_entries + F.nloc) * sizeof(C), st));
     const int nlev = (int)F.level_ptr.size() - 1;
+    size_t range = 0, ext = 0;
     for (int l = 0; l < nlev; ++l) {
         const int lo0 = F.level_ptr[l], hi = F.level_ptr[l + 1];
         C* sch_l = sch[l & 1];
@@ -368,39 +409,42 @@ void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const 
             front_assemble_kernel<C><<<nf, 256, 0, st>>>(F.level_fronts.p, lo, F.amap_front_ptr.p, F.amap_slot.p,
                                                          F.amap_pos.p, Bvals, ws);
             MWI_CHECK_LAUNCH();
-            // children sit one level deeper; their maximum update size bounds the grid
-            const int umax_child = l > 0 ? F.level_umax[l - 1] : 0;
-            if (umax_child > 0) {
-                dim3 blk(64, 4);
-                dim3 grd((umax_child + 3) / 4, nf);
-                for (int ci = 0; ci < 2; ++ci) {
-                    extend_add_kernel<C><<<grd, blk, 0, st>>>(F.level_fronts.p, lo, ci, F.child_ptr.p, F.child.p,
-                                                              F.p.p, F.u.p, F.f_off.p, F.sch_off.p, F.u_off.p,
-                                                              F.urel.p, ws, sch_child, sch_l);
+            for (int ci = 0; ci < 2; ++ci) {
+                MWI_REQUIRE(ext + 1 < F.ext_ptr.size(), MWI_EINVAL, "internal: extend-add tile list out of step");
+                const int64_t t0 = F.ext_ptr[ext], t1 = F.ext_ptr[ext + 1];
+                ++ext;
+                if (t1 > t0) {
+                    extend_add_kernel<C><<<(unsigned)(t1 - t0), dim3(64, 4), 0, st>>>(
+                        F.ext_tiles.p + t0, F.p.p, F.u.p, F.f_off.p, F.sch_off.p, F.u_off.p, F.urel.p, ws, sch_child,
+                        sch_l);
                     MWI_CHECK_LAUNCH();
                 }
             }
             const int pmax = F.level_pmax[l];
-            const int fmax = F.level_fmax[l];
             for (int k = 0; k < pmax; k += NB) {
-                panel_kernel<C, NB><<<nf, 256, 0, st>>>(F.level_fronts.p, lo, k, F.p.p, F.u.p, F.f_off.p, ws,
+                panel_kernel<C, NB><<<nf, 128, 0, st>>>(F.level_fronts.p, lo, k, F.p.p, F.u.p, F.f_off.p, ws,
                                                         perturbed);
                 MWI_CHECK_LAUNCH();
-                const int nrem = fmax - k - 1;
-                if (nrem <= 0) continue;
-                const int T = (nrem + TILE - 1) / TILE;
-                update_kernel<C, TILE, NB><<<dim3(T, T, nf), 256, 0, st>>>(F.level_fronts.p, lo, k, F.p.p, F.u.p,
-                                                                           F.f_off.p, F.sch_off.p, ws, sch_l);
-                MWI_CHECK_LAUNCH();
+                MWI_REQUIRE(range + 1 < ut.ptr.size(), MWI_EINVAL, "internal: update tile list out of step");
+                const int64_t t0 = ut.ptr[range], t1 = ut.ptr[range + 1];
+                ++range;
+                if (t1 > t0) {
+                    update_kernel<C, TILE, NB><<<(unsigned)(t1 - t0), 256, 0, st>>>(
+                        ut.tiles.p + t0, k, F.p.p, F.u.p, F.f_off.p, F.sch_off.p, ws, sch_l);
+                    MWI_CHECK_LAUNCH();
+                }
             }
             invert_level<C>(F, l, lo, nf, ws, inv_tmp, st);
         }
     }
 }
 
-template void factorize_fronts<float2>(const FrontsDev&, const double2*, float2*, float2* const[2], float2*, int*,
-                                       cudaStream_t);
-template void factorize_fronts<double2>(const FrontsDev&, const double2*, double2*, double2* const[2], double2*,
-                                        int*, cudaStream_t);
+template void factorize_fronts<float2>(const FrontsDev&, const UpdateTiles&, const double2*, float2*,
+                                       float2* const[2], float2*, int*, cudaStream_t);
+template void factorize_fronts<double2>(const FrontsDev&, const UpdateTiles&, const double2*, double2*,
+                                        double2* const[2], double2*, int*, cudaStream_t);
+
+int factor_block_cols(bool fp32) { return fp32 ? FactorCfg<float2>::NB : FactorCfg<double2>::NB; }
+int factor_tile_rows(bool fp32) { return fp32 ? FactorCfg<float2>::TILE : FactorCfg<double2>::TILE; }
 
 }  // namespace mwi

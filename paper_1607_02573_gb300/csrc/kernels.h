@@ -84,6 +84,10 @@ struct FrontsDev {
     DevBuf<int64_t> asm_base, asm_ptr;   // gather lists of the sweeps' extend-add
     DevBuf<int32_t> asm_src;
     DevBuf<int2> asm2;                   // the same lists as (source, source) per front row, -1 = none
+    // extend-add tiles (front, child, first of four child rows), per level and
+    // chunk of 65535 fronts: first children, then second children
+    DevBuf<int4> ext_tiles;
+    std::vector<int64_t> ext_ptr;
     DevBuf<int64_t> amap_front_ptr, amap_slot, amap_pos;
     DevBuf<int32_t> level_fronts;
     std::vector<int32_t> level_ptr;   // host copy
@@ -107,10 +111,22 @@ struct FrontsDev {
     int64_t inv_entries = 0;           // largest sum of f p over a level
 };
 
+// Trailing-update tiles (front, tile row, tile column <= row) of every step
+// of the blocked factorisation, in the order the factorisation consumes them
+// (levels, chunks of 65535 fronts, steps of nb pivot columns); ptr holds the
+// ranges.
+struct UpdateTiles {
+    int nb = 0, tile = 0;
+    DevBuf<int4> tiles;
+    std::vector<int64_t> ptr;
+};
+int factor_block_cols(bool fp32);
+int factor_tile_rows(bool fp32);
+
 // ws: factor store (panels); sch[2]: transient Schur buffers (even / odd levels)
 template <typename C>
-void factorize_fronts(const FrontsDev& F, const double2* Bvals, C* ws, C* const sch[2], C* inv_tmp, int* perturbed,
-                      cudaStream_t st);
+void factorize_fronts(const FrontsDev& F, const UpdateTiles& ut, const double2* Bvals, C* ws, C* const sch[2],
+                      C* inv_tmp, int* perturbed, cudaStream_t st);
 
 // y = M^{-1} x; scratch: Y, Z [nloc][m], upd [upd_rows][m]; tc selects the
 // complex FP32 sweep engine (0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores TF32)
