@@ -44,7 +44,9 @@ struct Gmres {
 // whose preconditioned directions Z are complex FP32 (the preconditioner's
 // own output, so stored exactly).  Arnoldi relation, residual and iterate
 // carry about 48 significant bits on the FP32 pipes; the Gram-Schmidt
-// coefficients are formed from the FP32 heads.
+// coefficients are formed from the FP32 heads, with one reduction and one
+// fused update pass per step (classical Gram-Schmidt with delayed
+// reorthogonalisation).
 struct GmresDF {
     // w = A z (z exact in FP32, w double-float planes)
     typedef std::function<void(const float2*, float2*)> OpA;
@@ -53,9 +55,9 @@ struct GmresDF {
     int64_t n = 0;
     int m = 0, restart = 0;
     DevBuf<float2> V, Z, W;
-    DevBuf<float4> hdf, ydf;
+    DevBuf<float4> hdf, hdf2, scal, ydf;   // double-float coefficients of the fused updates
     DevBuf<float2> invdf;
-    DevBuf<double2> H, cs, sn, g, y, h, hacc, partial;
+    DevBuf<double2> H, Hp, cs, sn, g, y, h, partial;
     DevBuf<double> dvec;
     DevBuf<int> ivec;
     std::function<void(int, const std::function<void()>&)> timer;

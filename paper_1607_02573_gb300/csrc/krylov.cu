@@ -482,6 +482,272 @@ __global__ void join_c128_kernel(int64_t count, const float2* __restrict__ in, d
     a[e] = make_double2(df_join(h.x, l.x), df_join(h.y, l.y));
 }
 
+
+// ---------------------------------------------------------------- DCGS2 Arnoldi (double-float basis)
+// Classical Gram-Schmidt with delayed reorthogonalisation (the one-reduction
+// DCGS2 Arnoldi of Swirydowicz, Langou, Ananthan, Yang and Thomas, "Low
+// synchronization Gram-Schmidt and generalized minimal residual algorithms",
+// 2021): step k makes one pass of dot products over the basis for both the
+// new vector w = A z_k and the once-orthogonalised v_k, then one fused update
+// pass that reorthogonalises v_k into q_k and projects w into the next v_{k+1}.
+
+// partial[b][j][c], j < nq: conj(Q_j) x; nq + j: conj(Q_j) y; 2 nq: conj(x) x;
+// 2 nq + 1: conj(x) y; 2 nq + 2: conj(y) y (FP32 heads, FP32 sums per thread,
+// FP64 across threads); eight basis vectors per pass over the rows
+__global__ void __launch_bounds__(256) dots2_kernel(int64_t n, int m, int nq, const float2* __restrict__ V,
+                                                    int64_t vstride, const float2* __restrict__ X,
+                                                    const float2* __restrict__ Yv, double2* __restrict__ partial) {
+    __shared__ double2 red[8][8][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c = blockIdx.y * 32 + tx;
+    const int64_t stride = (int64_t)gridDim.x * 8;
+    const int nout = 2 * nq + 3;
+    // fixed-order sum over the eight row lanes of the values in red[.][q][tx]
+    auto flush = [&](int nv, int j0, int jstride) {
+        __syncthreads();
+        if (ty < nv && c < m) {
+            double sx = 0.0, sy = 0.0;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                sx += red[r][ty][tx].x;
+                sy += red[r][ty][tx].y;
+            }
+            partial[((int64_t)blockIdx.x * nout + j0 + ty * jstride) * m + c] = make_double2(sx, sy);
+        }
+        __syncthreads();
+    };
+    for (int q0 = 0; q0 < (nq > 0 ? nq : 1); q0 += 8) {
+        const int nqc = nq > 0 ? min(8, nq - q0) : 0;
+        const bool self = q0 == 0;
+        float2 A[8], B[8], G = make_float2(0.f, 0.f), D = G, O = G;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) A[q] = B[q] = make_float2(0.f, 0.f);
+        if (c < m) {
+            for (int64_t r = blockIdx.x * 8 + ty; r < n; r += stride) {
+                const float2 x = X[r * m + c], y = Yv[r * m + c];
+                if (self) {
+                    G.x += x.x * x.x + x.y * x.y;
+                    D.x += x.x * y.x + x.y * y.y;
+                    D.y += x.x * y.y - x.y * y.x;
+                    O.x += y.x * y.x + y.y * y.y;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < nqc) {
+                        const float2 v = V[(int64_t)(q0 + q) * vstride + r * m + c];
+                        A[q].x += v.x * x.x + v.y * x.y;
+                        A[q].y += v.x * x.y - v.y * x.x;
+                        B[q].x += v.x * y.x + v.y * y.y;
+                        B[q].y += v.x * y.y - v.y * y.x;
+                    }
+            }
+        }
+        if (nqc > 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[ty][q][tx] = make_double2(A[q].x, A[q].y);
+            flush(nqc, q0, 1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[ty][q][tx] = make_double2(B[q].x, B[q].y);
+            flush(nqc, nq + q0, 1);
+        }
+        if (self) {
+            red[ty][0][tx] = make_double2(G.x, 0.0);
+            red[ty][1][tx] = make_double2(D.x, D.y);
+            red[ty][2][tx] = make_double2(O.x, 0.0);
+            flush(3, 2 * nq, 1);
+        }
+    }
+}
+
+// Per column: finalise column k-1 of the Hessenberg matrix with v_k's
+// reorthogonalisation (coefficients a, norm nu), form column k from w's
+// projections (provisional: its last entry rho_k is the Pythagorean norm of
+// the projected w, made exact by the next step's correction), test the
+// residual estimate with a provisional rotation of column k, and emit the
+// double-float coefficients of the fused update.  A column that converges (or
+// the last step) keeps column k as it stands: v_{k+1} then closes the basis
+// without reorthogonalisation, which leaves the Arnoldi relation exact.
+__device__ __forceinline__ double2 conjmul(double2 a, double2 b) { return cmul(cconj(a), b); }
+
+__device__ void finalize_column(int m, int c, int j, int restart, double2* __restrict__ Hj,
+                                double2* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ g) {
+    for (int i = 0; i < j; ++i) {
+        const double2 ci = cs[i * m + c], si = sn[i * m + c];
+        const double2 a = Hj[i * m + c], b = Hj[(i + 1) * m + c];
+        Hj[i * m + c] = cadd(cmul(ci, a), cmul(si, b));
+        Hj[(i + 1) * m + c] = csub(cmul(cconj(ci), b), cmul(cconj(si), a));
+    }
+    const double2 a = Hj[j * m + c], b = Hj[(j + 1) * m + c];
+    const double den = sqrt(cabs2(a) + cabs2(b));
+    double2 cj, sj;
+    if (den > 0.0) { cj = cscale(cconj(a), 1.0 / den); sj = cscale(cconj(b), 1.0 / den); }
+    else { cj = make_double2(1.0, 0.0); sj = make_double2(0.0, 0.0); }
+    cs[j * m + c] = cj;
+    sn[j * m + c] = sj;
+    Hj[j * m + c] = make_double2(den, 0.0);
+    Hj[(j + 1) * m + c] = make_double2(0.0, 0.0);
+    const double2 gj = g[j * m + c];
+    g[(j + 1) * m + c] = cscale(cmul(cconj(sj), gj), -1.0);
+    g[j * m + c] = cmul(cj, gj);
+    (void)restart;
+}
+
+__device__ __forceinline__ float4 df4(double2 v) {
+    const float2 a = df_split(v.x), b = df_split(v.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+__global__ void arnoldi_dcgs_kernel(int m, int k, int restart, int last, const double2* __restrict__ dots,
+                                    double2* __restrict__ H, double2* __restrict__ Hp, double2* __restrict__ cs,
+                                    double2* __restrict__ sn, double2* __restrict__ g, int* __restrict__ active,
+                                    int* __restrict__ kcol, const double* __restrict__ tol,
+                                    double* __restrict__ resid, double* __restrict__ rho,
+                                    int* __restrict__ n_active, float4* __restrict__ coefQ,
+                                    float4* __restrict__ coefW, float4* __restrict__ scal) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    const int nq = k, nout = 2 * nq + 3;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!active[c]) {
+        for (int i = 0; i < nq; ++i) coefQ[i * m + c] = coefW[i * m + c] = z4;
+        scal[c] = scal[m + c] = z4;
+        return;
+    }
+    const double2* a = dots;               // a_i = conj(q_i) v_k
+    const double2* b = dots + nq * m;      // b_i = conj(q_i) w
+    const double gam = dots[(2 * nq) * m + c].x;
+    const double2 del = dots[(2 * nq + 1) * m + c];
+    const double om = dots[(2 * nq + 2) * m + c].x;
+    double nu = 1.0;
+    if (k > 0) {
+        double a2 = 0.0;
+        for (int i = 0; i < nq; ++i) a2 += cabs2(a[i * m + c]);
+        nu = sqrt(fmax(gam - a2, 1e-30 * fmax(gam, 1e-300)));
+        // column k-1: v_k = Q a + nu q_k, so h(i, k-1) += rho_{k-1} a_i and h(k, k-1) = rho_{k-1} nu
+        const double r1 = rho[c];
+        double2* Hc = H + (int64_t)(k - 1) * (restart + 1) * m;
+        const double2* Pc = Hp;
+        for (int i = 0; i < k; ++i) Hc[i * m + c] = cadd(Pc[i * m + c], cscale(a[i * m + c], r1));
+        Hc[k * m + c] = make_double2(r1 * nu, 0.0);
+        finalize_column(m, c, k - 1, restart, Hc, cs, sn, g);
+    }
+    // q_k^H w and the projected w's norm
+    double2 ab = make_double2(0.0, 0.0);
+    double b2 = 0.0;
+    for (int i = 0; i < nq; ++i) {
+        ab = cadd(ab, conjmul(a[i * m + c], b[i * m + c]));
+        b2 += cabs2(b[i * m + c]);
+    }
+    const double2 ck = cscale(csub(del, ab), 1.0 / nu);
+    const double rk = sqrt(fmax(om - b2 - cabs2(ck), 1e-14 * om));
+    // provisional column k: (b_0 .. b_{k-1}, c_k, rho_k)
+    for (int i = 0; i < nq; ++i) Hp[i * m + c] = b[i * m + c];
+    Hp[k * m + c] = ck;
+    Hp[(k + 1) * m + c] = make_double2(rk, 0.0);
+    // its rotated entry k (rotations 0..k-1), then the provisional residual
+    double2 t = nq > 0 ? b[c] : ck;
+    for (int i = 0; i < k; ++i) {
+        const double2 nxt = i + 1 < k ? b[(i + 1) * m + c] : ck;
+        const double2 ci = cs[i * m + c], si = sn[i * m + c];
+        t = csub(cmul(cconj(ci), nxt), cmul(cconj(si), t));
+    }
+    const double den = sqrt(cabs2(t) + rk * rk);
+    const double rr = den > 0.0 ? rk / den * sqrt(cabs2(g[k * m + c])) : 0.0;
+    resid[c] = rr;
+    rho[c] = rk;
+    const bool stop = rr <= tol[c] || !(rr == rr) || rk == 0.0 || last;
+    if (stop) {
+        double2* Hc = H + (int64_t)k * (restart + 1) * m;
+        for (int i = 0; i <= k + 1; ++i) Hc[i * m + c] = Hp[i * m + c];
+        finalize_column(m, c, k, restart, Hc, cs, sn, g);
+        kcol[c] = k + 1;
+        if (!last) active[c] = 0;
+        else if (!(rr <= tol[c])) atomicAdd(n_active, 1);
+    } else {
+        kcol[c] = k;
+        atomicAdd(n_active, 1);
+    }
+    // fused update: q_k = v_k / nu - sum_i q_i a_i / nu;
+    // v_{k+1} = w / rho_k - sum_i q_i (b_i - a_i c_k / nu) / rho_k - v_k c_k / (nu rho_k)
+    const double inu = 1.0 / nu, irk = 1.0 / rk;
+    for (int i = 0; i < nq; ++i) {
+        const double2 ai = a[i * m + c];
+        coefQ[i * m + c] = df4(cscale(ai, -inu));
+        coefW[i * m + c] = df4(cscale(csub(b[i * m + c], cscale(cmul(ai, ck), inu)), -irk));
+    }
+    scal[c] = df4(make_double2(k > 0 ? inu : 1.0, irk));         // (1 / nu, 1 / rho_k) as reals
+    scal[m + c] = df4(cscale(ck, -inu * irk));                     // -c_k / (nu rho_k)
+}
+
+// q_k (into V slot k, when k > 0) and v_{k+1} (into V slot k + 1) in one pass
+// over the basis: per element, two double-float accumulators over the k basis
+// vectors, v_k and w
+__global__ void __launch_bounds__(256) dcgs_update_df_kernel(int64_t nm, int m, int k, float2* __restrict__ V,
+                                                             int64_t vstride, const float2* __restrict__ W,
+                                                             const float4* __restrict__ coefQ,
+                                                             const float4* __restrict__ coefW,
+                                                             const float4* __restrict__ scal, int write_next) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nm) return;
+    const int c = (int)(e % m);
+    const float4 s1 = scal[c], s2 = scal[m + c];
+    float2* vk = V + (int64_t)k * vstride;
+    const float2 vh = vk[e], vl = vk[nm + e], wh = W[e], wl = W[nm + e];
+    // q accumulator: v_k / nu; w accumulator: w / rho_k + v_k (-c_k / (nu rho_k))
+    dfl qr = df_mul(vh.x, vl.x, s1.x, s1.y), qi = df_mul(vh.y, vl.y, s1.x, s1.y);
+    dfl wr = df_mul(wh.x, wl.x, s1.z, s1.w), wi = df_mul(wh.y, wl.y, s1.z, s1.w);
+    df_mac(wr, vh.x, vl.x, s2.x, s2.y);
+    df_mac(wr, -vh.y, -vl.y, s2.z, s2.w);
+    df_mac(wi, vh.x, vl.x, s2.z, s2.w);
+    df_mac(wi, vh.y, vl.y, s2.x, s2.y);
+    int i = 0;
+    for (; i + 2 <= k; i += 2) {
+        float2 qh[2], ql[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            qh[u] = V[(int64_t)(i + u) * vstride + e];
+            ql[u] = V[(int64_t)(i + u) * vstride + nm + e];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float4 a = coefQ[(i + u) * m + c], b = coefW[(i + u) * m + c];
+            df_mac(qr, qh[u].x, ql[u].x, a.x, a.y);
+            df_mac(qr, -qh[u].y, -ql[u].y, a.z, a.w);
+            df_mac(qi, qh[u].x, ql[u].x, a.z, a.w);
+            df_mac(qi, qh[u].y, ql[u].y, a.x, a.y);
+            df_mac(wr, qh[u].x, ql[u].x, b.x, b.y);
+            df_mac(wr, -qh[u].y, -ql[u].y, b.z, b.w);
+            df_mac(wi, qh[u].x, ql[u].x, b.z, b.w);
+            df_mac(wi, qh[u].y, ql[u].y, b.x, b.y);
+        }
+    }
+    for (; i < k; ++i) {
+        const float2 qh = V[(int64_t)i * vstride + e], ql = V[(int64_t)i * vstride + nm + e];
+        const float4 a = coefQ[i * m + c], b = coefW[i * m + c];
+        df_mac(qr, qh.x, ql.x, a.x, a.y);
+        df_mac(qr, -qh.y, -ql.y, a.z, a.w);
+        df_mac(qi, qh.x, ql.x, a.z, a.w);
+        df_mac(qi, qh.y, ql.y, a.x, a.y);
+        df_mac(wr, qh.x, ql.x, b.x, b.y);
+        df_mac(wr, -qh.y, -ql.y, b.z, b.w);
+        df_mac(wi, qh.x, ql.x, b.z, b.w);
+        df_mac(wi, qh.y, ql.y, b.x, b.y);
+    }
+    if (k > 0) {
+        qr = df_norm(qr);
+        qi = df_norm(qi);
+        vk[e] = make_float2(qr.h, qi.h);
+        vk[nm + e] = make_float2(qr.l, qi.l);
+    }
+    if (write_next) {
+        wr = df_norm(wr);
+        wi = df_norm(wi);
+        float2* vn = V + (int64_t)(k + 1) * vstride;
+        vn[e] = make_float2(wr.h, wi.h);
+        vn[nm + e] = make_float2(wr.l, wi.l);
+    }
+}
+
 // ----------------------------------------------------------------------------
 static inline unsigned nblocks(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
 
@@ -613,10 +879,12 @@ void GmresDF::reserve(int64_t n_, int m_, int restart_) {
     sn.ensure((size_t)restart * m);
     g.ensure((size_t)(restart + 1) * m);
     y.ensure((size_t)restart * m);
-    h.ensure((size_t)(restart + 2) * m);
-    hacc.ensure((size_t)(restart + 1) * m);
-    partial.ensure((size_t)kDotBlocks * (restart + 2) * m);
+    h.ensure((size_t)(2 * restart + 3) * m);
+    partial.ensure((size_t)kDotBlocks * (2 * restart + 3) * m);
     hdf.ensure((size_t)(restart + 1) * m);
+    hdf2.ensure((size_t)(restart + 1) * m);
+    scal.ensure((size_t)2 * m);
+    Hp.ensure((size_t)(restart + 2) * m);
     ydf.ensure((size_t)restart * m);
     invdf.ensure((size_t)m);
     dvec.ensure((size_t)8 * m);
@@ -636,13 +904,14 @@ int GmresDF::cycle(const OpA& A, const OpM& M, const float2* r0, float2* x, cons
     double* beta2 = dvec.p;
     double* inv = dvec.p + m;
     double* resid = dvec.p + 2 * m;
-    double* hn2 = dvec.p + 3 * m;
+    double* rho = dvec.p + 3 * m;
     int* active = ivec.p;
     int* kcol = ivec.p + m;
     int* nact = ivec.p + 4 * m;
     norms2(r0, beta2, st);
     cycle_start_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, beta2, tol, active, kcol, g.p, inv, resid, invdf.p);
     MWI_CHECK_LAUNCH();
+    // v_0 = r0 / beta exactly (q_0 = v_0: no reorthogonalisation at step 0)
     scale_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, r0, invdf.p, V.p);
     MWI_CHECK_LAUNCH();
     int k = 0;
@@ -650,32 +919,29 @@ int GmresDF::cycle(const OpA& A, const OpM& M, const float2* r0, float2* x, cons
     for (; k < max_steps; ++k) {
         float2* vk = V.p + (int64_t)k * vs;
         float2* zk = Z.p + (int64_t)k * nm;
-        // the preconditioner sees the FP32 head of v_k; z_k is stored exactly
+        // the preconditioner sees the FP32 head of v_k (once orthogonalised);
+        // z_k is stored exactly
         M(vk, zk);
         A(zk, W.p);
-        // CGS2: coefficients from the FP32 heads (their rounding only costs
-        // orthogonality at the 1e-7 level, which the second pass keeps from
-        // growing), updates in double-float so that A z_k = V h holds to
-        // double-float accuracy
+        const int last = k + 1 == max_steps ? 1 : 0;
         auto ortho = [&] {
-            MWI_CUDA(cudaMemsetAsync(hacc.p, 0, (size_t)(k + 1) * m * sizeof(double2), st));
-            for (int pass = 0; pass < 2; ++pass) {
-                dots_launch<float2>(n, m, V.p, k + 1, vs, W.p, partial.p, h.p, hacc.p, hdf.p, st, 0);
-                cgs_update_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, k + 1, V.p, vs, hdf.p, W.p);
-                MWI_CHECK_LAUNCH();
-            }
-            norms2(W.p, hn2, st);
+            dim3 blk(32, 8), grd(kDotBlocks, (m + 31) / 32);
+            dots2_kernel<<<grd, blk, 0, st>>>(n, m, k, V.p, vs, vk, W.p, partial.p);
+            MWI_CHECK_LAUNCH();
+            const int nout = 2 * k + 3;
+            dots_reduce_kernel<<<nout, 256, 0, st>>>(kDotBlocks, nout, 0, m, partial.p, h.p, nullptr, nullptr);
+            MWI_CHECK_LAUNCH();
+            MWI_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), st));
+            arnoldi_dcgs_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, k, restart, last, h.p, H.p, Hp.p, cs.p, sn.p,
+                                                                 g.p, active, kcol, tol, resid, rho, nact, hdf.p,
+                                                                 hdf2.p, scal.p);
+            MWI_CHECK_LAUNCH();
+            dcgs_update_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, k, V.p, vs, W.p, hdf.p, hdf2.p, scal.p,
+                                                                    last ? 0 : 1);
+            MWI_CHECK_LAUNCH();
         };
         if (timer) timer(2, ortho);
         else ortho();
-        MWI_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), st));
-        arnoldi_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, k, restart, hacc.p, hn2, H.p, cs.p, sn.p, g.p, active,
-                                                        kcol, tol, resid, inv, nact, invdf.p);
-        MWI_CHECK_LAUNCH();
-        if (k + 1 < max_steps) {
-            scale_df_kernel<<<nblocks(nm, 256), 256, 0, st>>>(nm, m, W.p, invdf.p, V.p + (int64_t)(k + 1) * vs);
-            MWI_CHECK_LAUNCH();
-        }
         MWI_CUDA(cudaMemcpyAsync(&n_active_host, nact, sizeof(int), cudaMemcpyDeviceToHost, st));
         MWI_CUDA(cudaStreamSynchronize(st));
         if (n_active_host == 0) { ++k; break; }
