@@ -245,6 +245,17 @@ mwi_status mwi_decomposition(mwi_problem_t prob, int32_t* part, int64_t* n_local
 mwi_status mwi_factor_stats(mwi_problem_t prob, int64_t* factor_entries, int64_t* n_fronts,
                             int64_t* max_front, double* factor_flops);
 
+/* Algorithmic memory traffic of one ORAS application (Eq. ORAS) to m columns,
+ * in bytes, for the roofline of the sweeps (no counterpart in the paper; a
+ * measurement aid): every stored factor entry read once per sweep (the unit
+ * lower triangles of L11^-1 and the blocks -L21 L11^-1) plus D^-1, and the
+ * vectors each step must move -- the gather of x into the local vectors, per
+ * front the pivot rows read and written in both sweeps, the update rows
+ * written once and read by the parent (forward) and the ancestor rows read
+ * (backward), and the weighted scatter into y.  Entries count 8 bytes in the
+ * complex FP32 modes and 16 in FP64. */
+mwi_status mwi_oras_traffic(mwi_problem_t prob, int32_t m, double* bytes);
+
 /* Per-kernel timing since the last reset, from CUDA events recorded on the
  * problem's stream around every call (no synchronisation in between):
  * ms[0] SpMM, ms[1] ORAS apply, ms[2] orthogonalisation (CGS2 + norms),

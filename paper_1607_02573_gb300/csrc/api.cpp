@@ -1111,6 +1111,26 @@ mwi_status mwi_factor_stats(mwi_problem_t P, int64_t* factor_entries, int64_t* n
     });
 }
 
+mwi_status mwi_oras_traffic(mwi_problem_t P, int32_t m, double* bytes) {
+    return guard([&] {
+        MWI_REQUIRE(P && bytes, MWI_EINVAL, "null argument");
+        MWI_REQUIRE(m > 0, MWI_EINVAL, "m must be positive");
+        const Decomposition& D = P->dec->D;
+        const double e = P->opts.precision == 0 ? 16.0 : 8.0;  // bytes per stored complex entry
+        double factor = 0.0, rows = 0.0;
+        for (size_t s = 0; s < D.fronts.size(); ++s) {
+            const Front& fr = D.fronts[s];
+            const double p = fr.p, u = fr.u;
+            factor += 2.0 * (p * (p + 1.0) / 2.0 + u * p) + p;  // both sweeps, plus D^-1
+            double uc = 0.0;
+            for (int32_t q = D.child_ptr[s]; q < D.child_ptr[s + 1]; ++q) uc += D.fronts[D.child[q]].u;
+            rows += (p + uc + p + u) + (p + u + p);              // forward, backward
+        }
+        const double n = (double)P->mesh->T.ndof, nloc = (double)D.sub_off[D.n_sub];
+        *bytes = factor * e + (rows + 2.0 * (n + nloc)) * m * e;  // + gather and scatter
+    });
+}
+
 mwi_status mwi_kernel_times(mwi_problem_t P, double* ms, int64_t* counts, int32_t reset) {
     return guard([&] {
         MWI_REQUIRE(P, MWI_EINVAL, "null problem");

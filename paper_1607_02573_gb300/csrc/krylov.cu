@@ -523,22 +523,34 @@ __global__ void __launch_bounds__(256) dots2_kernel(int64_t n, int m, int nq, co
 #pragma unroll
         for (int q = 0; q < 8; ++q) A[q] = B[q] = make_float2(0.f, 0.f);
         if (c < m) {
-            for (int64_t r = blockIdx.x * 8 + ty; r < n; r += stride) {
-                const float2 x = X[r * m + c], y = Yv[r * m + c];
+            // two rows per iteration, their loads issued together
+            for (int64_t r = blockIdx.x * 8 + ty; r < n; r += 2 * stride) {
+                const bool two = r + stride < n;
+                const int64_t r2 = two ? r + stride : r;
+                const float2 x0 = X[r * m + c], y0 = Yv[r * m + c];
+                const float2 x1 = two ? X[r2 * m + c] : make_float2(0.f, 0.f);
+                const float2 y1 = two ? Yv[r2 * m + c] : make_float2(0.f, 0.f);
+                float2 v0[8], v1[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < nqc) {
+                        const float2* Vq = V + (int64_t)(q0 + q) * vstride + c;
+                        v0[q] = Vq[r * m];
+                        v1[q] = two ? Vq[r2 * m] : make_float2(0.f, 0.f);
+                    }
                 if (self) {
-                    G.x += x.x * x.x + x.y * x.y;
-                    D.x += x.x * y.x + x.y * y.y;
-                    D.y += x.x * y.y - x.y * y.x;
-                    O.x += y.x * y.x + y.y * y.y;
+                    G.x += x0.x * x0.x + x0.y * x0.y + x1.x * x1.x + x1.y * x1.y;
+                    D.x += x0.x * y0.x + x0.y * y0.y + x1.x * y1.x + x1.y * y1.y;
+                    D.y += x0.x * y0.y - x0.y * y0.x + x1.x * y1.y - x1.y * y1.x;
+                    O.x += y0.x * y0.x + y0.y * y0.y + y1.x * y1.x + y1.y * y1.y;
                 }
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
                     if (q < nqc) {
-                        const float2 v = V[(int64_t)(q0 + q) * vstride + r * m + c];
-                        A[q].x += v.x * x.x + v.y * x.y;
-                        A[q].y += v.x * x.y - v.y * x.x;
-                        B[q].x += v.x * y.x + v.y * y.y;
-                        B[q].y += v.x * y.y - v.y * y.x;
+                        A[q].x += v0[q].x * x0.x + v0[q].y * x0.y + v1[q].x * x1.x + v1[q].y * x1.y;
+                        A[q].y += v0[q].x * x0.y - v0[q].y * x0.x + v1[q].x * x1.y - v1[q].y * x1.x;
+                        B[q].x += v0[q].x * y0.x + v0[q].y * y0.y + v1[q].x * y1.x + v1[q].y * y1.y;
+                        B[q].y += v0[q].x * y0.y - v0[q].y * y0.x + v1[q].x * y1.y - v1[q].y * y1.x;
                     }
             }
         }
@@ -925,11 +937,13 @@ int GmresDF::cycle(const OpA& A, const OpM& M, const float2* r0, float2* x, cons
         A(zk, W.p);
         const int last = k + 1 == max_steps ? 1 : 0;
         auto ortho = [&] {
-            dim3 blk(32, 8), grd(kDotBlocks, (m + 31) / 32);
+            // one wave: two resident blocks per SM at this kernel's register use
+            const int nblk = kDotBlocks / 2;
+            dim3 blk(32, 8), grd(nblk, (m + 31) / 32);
             dots2_kernel<<<grd, blk, 0, st>>>(n, m, k, V.p, vs, vk, W.p, partial.p);
             MWI_CHECK_LAUNCH();
             const int nout = 2 * k + 3;
-            dots_reduce_kernel<<<nout, 256, 0, st>>>(kDotBlocks, nout, 0, m, partial.p, h.p, nullptr, nullptr);
+            dots_reduce_kernel<<<nout, 256, 0, st>>>(nblk, nout, 0, m, partial.p, h.p, nullptr, nullptr);
             MWI_CHECK_LAUNCH();
             MWI_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), st));
             arnoldi_dcgs_kernel<<<nblocks(m, 128), 128, 0, st>>>(m, k, restart, last, h.p, H.p, Hp.p, cs.p, sn.p,

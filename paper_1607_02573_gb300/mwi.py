@@ -76,6 +76,7 @@ _SIGS = {
     "mwi_matrix_csr": [_vp, _i64p, _i64p, _i32p, _dp],
     "mwi_decomposition": [_vp, _i32p, _i64p],
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
+    "mwi_oras_traffic": [_vp, C.c_int32, _dp],
     "mwi_kernel_times": [_vp, _dp, _i64p, C.c_int32],
     "mwi_misfit": [_vp, _dp, _dp, _dp],
 }
@@ -270,6 +271,12 @@ class Problem:
         d = C.c_double()
         check(mwi_factor_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         return dict(factor_entries=a.value, n_fronts=b.value, max_front=c.value, factor_flops=d.value)
+
+    def oras_traffic(self, m):
+        """Algorithmic bytes of one ORAS application to m columns."""
+        b = C.c_double()
+        check(mwi_oras_traffic(self.h, m, C.byref(b)))
+        return b.value
 
     def kernel_times(self, reset=True):
         ms = np.zeros(4)

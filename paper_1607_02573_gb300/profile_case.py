@@ -42,6 +42,7 @@ def main(argv):
     print(f"mesh {t1 - t0:.1f} s, assemble+decompose+factorise {t2 - t1:.1f} s, forward {t3 - t2:.2f} s "
           f"({ants.shape[0] / (t3 - t2):.1f} RHS-solves/s)")
     print("factor", P.factor_stats())
+    print("oras_bytes_per_call", P.oras_traffic(min(32, ants.shape[0])))
     print("solve", info)
     print("reciprocity", float(np.linalg.norm(S - S.T) / np.linalg.norm(S)))
     P.close()
