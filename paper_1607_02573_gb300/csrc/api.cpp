@@ -40,9 +40,11 @@ struct DecompEntry {
 // the lower-triangle tiles of every front of the chunk with k < p.
 void build_update_tiles(const Decomposition& D, int nb, int tile, UpdateTiles& ut, cudaStream_t st) {
     std::vector<int4> t;
+    std::vector<int2> rt;
     ut.nb = nb;
     ut.tile = tile;
     ut.ptr.assign(1, 0);
+    ut.rptr.assign(1, 0);
     for (int l = 0; l < D.n_levels; ++l) {
         const int lo0 = D.level_ptr[l], hi = D.level_ptr[l + 1];
         int pmax = 0;
@@ -58,13 +60,17 @@ void build_update_tiles(const Decomposition& D, int nb, int tile, UpdateTiles& u
                     const int T = (int)((nrem + tile - 1) / tile);
                     for (int bi = 0; bi < T; ++bi)
                         for (int bj = 0; bj <= bi; ++bj) t.push_back(make_int4(s, bi, bj, 0));
+                    for (int r = k + std::min(nb, fr.p - k); r < fr.p + fr.u; r += 128) rt.push_back(make_int2(s, r));
                 }
                 ut.ptr.push_back((int64_t)t.size());
+                ut.rptr.push_back((int64_t)rt.size());
             }
         }
     }
     if (t.empty()) t.push_back(make_int4(0, 0, 0, 0));
+    if (rt.empty()) rt.push_back(make_int2(0, 0));
     ut.tiles.upload(t, st);
+    ut.rtiles.upload(rt, st);
     MWI_CUDA(cudaStreamSynchronize(st));
 }
 

@@ -79,102 +79,120 @@ __device__ __forceinline__ bool bad_pivot(C d) {
     return !(a > (typename real_of<C>::type)0) || !isfinite(a);
 }
 
-// Panel k..k+nb of every front of the level: factor the diagonal block in
-// shared memory (L unit lower, D on the diagonal), form M = L^{-T} D^{-1}
-// there, then every row below is L_i = a_i M (a_i = that row of the block
-// column): a small dense product, eight output columns at a time.
+// Panel step k, part 1: the nb x nb diagonal block of every front of the
+// level, one warp per front (lane r owns row r): LDL^T in shared memory, then
+// M = L^{-T} D^{-1} (upper triangular) by back substitution, lane j taking
+// column j.  The factorised block goes back to the panel (L below the
+// diagonal, D on it) and M's strictly upper part into the block's upper
+// triangle, which the factorisation does not use otherwise (it is cleared when
+// the panel is replaced by its partitioned inverse).
 template <typename C, int NB>
-__global__ void __launch_bounds__(128) panel_kernel(const int32_t* __restrict__ level_fronts, int lo, int k,
-                                                    const int32_t* __restrict__ P, const int32_t* __restrict__ U,
-                                                    const int64_t* __restrict__ f_off, C* __restrict__ ws,
-                                                    int* __restrict__ perturbed) {
-    const int s = level_fronts[lo + blockIdx.x];
+__global__ void __launch_bounds__(128) panel_diag_kernel(const int32_t* __restrict__ level_fronts, int lo, int nf,
+                                                         int k, const int32_t* __restrict__ P,
+                                                         const int32_t* __restrict__ U,
+                                                         const int64_t* __restrict__ f_off, C* __restrict__ ws,
+                                                         int* __restrict__ perturbed) {
+    __shared__ C Dgs[4][NB][NB + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 4 + warp;
+    if (q >= nf) return;
+    const int s = level_fronts[lo + q];
     const int p = P[s];
     if (k >= p) return;
     const int64_t f = (int64_t)p + U[s];
     const int nb = min(NB, p - k);
     C* F = ws + f_off[s];
-    __shared__ C Dg[NB][NB + 1];
-    __shared__ C M[NB][NB + 1];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int r = e % NB, c = e / NB;
+    C (*Dg)[NB + 1] = Dgs[warp];
+    for (int e = lane; e < NB * NB; e += 32) {
+        const int r = e % NB, c = e / NB;
         Dg[r][c] = (r < nb && c < nb && r >= c) ? F[(int64_t)(k + c) * f + k + r] : czero<C>();
     }
-    __syncthreads();
-    // the diagonal block, by the first warp alone (lane r owns row r)
-    if (tid < 32) {
-        const int r = tid;
-        for (int j = 0; j < nb; ++j) {
-            C d = Dg[j][j];
-            if (bad_pivot(d)) {  // the same value in every lane
-                __syncwarp();
-                if (r == 0) {
-                    Dg[j][j] = cmake<C>(1, 0);
-                    atomicAdd(perturbed, 1);
-                }
-                d = cmake<C>(1, 0);
-            }
-            const bool below = r > j && r < nb;
-            C ld = czero<C>();
-            if (below) {
-                const C l = cmul(Dg[r][j], crecip(d));  // l_rj = a_rj / d_j
-                Dg[r][j] = l;
-                ld = cmul(l, d);
-            }
+    __syncwarp();
+    const int r = lane;
+    for (int j = 0; j < nb; ++j) {
+        C d = Dg[j][j];
+        if (bad_pivot(d)) {  // the same value in every lane
             __syncwarp();
-            if (below)
-                for (int c = j + 1; c <= r; ++c) Dg[r][c] = csub(Dg[r][c], cmul(ld, Dg[c][j]));
-            __syncwarp();
+            if (r == 0) {
+                Dg[j][j] = cmake<C>(1, 0);
+                atomicAdd(perturbed, 1);
+            }
+            d = cmake<C>(1, 0);
+        }
+        const bool below = r > j && r < nb;
+        C ld = czero<C>();
+        if (below) {
+            const C l = cmul(Dg[r][j], crecip(d));  // l_rj = a_rj / d_j
+            Dg[r][j] = l;
+            ld = cmul(l, d);
+        }
+        __syncwarp();
+        if (below)
+            for (int c = j + 1; c <= r; ++c) Dg[r][c] = csub(Dg[r][c], cmul(ld, Dg[c][j]));
+        __syncwarp();
+    }
+    // column j of M (lane j): y_j = 1, y_r = -sum_{c=r+1..j} L(c, r) y_c for r < j,
+    // kept unscaled in the upper triangle, then scaled by 1 / d_j
+    if (r < nb) {
+        const int j = r;
+        for (int i = j - 1; i >= 0; --i) {
+            C y = cmake<C>(-Dg[j][i].x, -Dg[j][i].y);
+            for (int c = i + 1; c < j; ++c) y = cfms(Dg[c][i], Dg[c][j], y);
+            Dg[i][j] = y;
         }
     }
-    __syncthreads();
-    // column j of M: y = L^{-T} e_j by back substitution, scaled by 1 / d_j
-    // (zero below the diagonal and outside the nb x nb block)
-    if (tid < NB) {
-        const int j = tid;
-        for (int r = NB - 1; r >= 0; --r) {
-            C y = czero<C>();
-            if (j < nb && r <= j) {
-                if (r == j) {
-                    y = cmake<C>(1, 0);
-                } else {
-                    for (int c = r + 1; c <= j; ++c) y = cfms(Dg[c][r], M[c][j], y);
-                }
-            }
-            M[r][j] = y;
+    __syncwarp();
+    for (int e = lane; e < nb * nb; e += 32) {
+        const int rr = e % nb, c = e / nb;
+        C v = Dg[rr][c];
+        if (rr < c) v = cmul(v, crecip(Dg[c][c]));
+        F[(int64_t)(k + c) * f + k + rr] = v;
+    }
+}
+
+// Panel step k, part 2: the rows below the diagonal block, L_i = a_i M, one
+// thread per row over a tile list (front, first row) of 128-row tiles; M is
+// rebuilt from the block (its strictly upper part, and 1 / D on the diagonal)
+template <typename C, int NB>
+__global__ void __launch_bounds__(128) panel_rows_kernel(const int2* __restrict__ tiles, int k,
+                                                         const int32_t* __restrict__ P, const int32_t* __restrict__ U,
+                                                         const int64_t* __restrict__ f_off, C* __restrict__ ws) {
+    __shared__ C M[NB][NB + 1];
+    const int2 tl = tiles[blockIdx.x];
+    const int s = tl.x;
+    const int p = P[s];
+    const int64_t f = (int64_t)p + U[s];
+    const int nb = min(NB, p - k);
+    C* F = ws + f_off[s];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        C v = czero<C>();
+        if (r < nb && c < nb && r <= c) {
+            const C x = F[(int64_t)(k + c) * f + k + r];
+            v = r == c ? crecip(x) : x;
         }
-        if (j < nb) {
-            const C dj = crecip(Dg[j][j]);
-            for (int r = 0; r <= j; ++r) M[r][j] = cmul(M[r][j], dj);
-        }
+        M[r][c] = v;
     }
     __syncthreads();
-    // rows below the diagonal block: L_i = a_i M (M upper triangular): the
-    // row's output accumulates in registers while its entries stream in,
+    const int64_t i = (int64_t)tl.y + threadIdx.x;
+    if (i >= f) return;
+    // the row's output accumulates in registers while its entries stream in,
     // eight independent loads at a time
-    for (int64_t i = k + nb + tid; i < f; i += blockDim.x) {
-        C acc[NB];
+    C acc[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) acc[j] = czero<C>();
-        for (int c0 = 0; c0 < nb; c0 += 8) {
-            C a[8];
+    for (int j = 0; j < NB; ++j) acc[j] = czero<C>();
+    for (int c0 = 0; c0 < nb; c0 += 8) {
+        C a[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = c0 + q < nb ? F[(int64_t)(k + c0 + q) * f + i] : czero<C>();
+        for (int q = 0; q < 8; ++q) a[q] = c0 + q < nb ? F[(int64_t)(k + c0 + q) * f + i] : czero<C>();
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+        for (int q = 0; q < 8; ++q)
 #pragma unroll
-                for (int j = 0; j < NB; ++j) acc[j] = cfma(a[q], M[min(c0 + q, NB - 1)][j], acc[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (j < nb) F[(int64_t)(k + j) * f + i] = acc[j];
+            for (int j = 0; j < NB; ++j) acc[j] = cfma(a[q], M[min(c0 + q, NB - 1)][j], acc[j]);
     }
-    __syncthreads();
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-        int r = e % nb, c = e / nb;
-        if (r >= c) F[(int64_t)(k + c) * f + k + r] = Dg[r][c];
-    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < nb) F[(int64_t)(k + j) * f + i] = acc[j];
 }
 
 // Trailing update of the lower triangle: F[i][c] -= sum_j L[i][j] d_j L[c][j],
@@ -422,10 +440,19 @@ void factorize_fronts(const FrontsDev& F, const UpdateTiles& ut, const double2* 
             }
             const int pmax = F.level_pmax[l];
             for (int k = 0; k < pmax; k += NB) {
-                panel_kernel<C, NB><<<nf, 128, 0, st>>>(F.level_fronts.p, lo, k, F.p.p, F.u.p, F.f_off.p, ws,
-                                                        perturbed);
+                panel_diag_kernel<C, NB><<<(nf + 3) / 4, 128, 0, st>>>(F.level_fronts.p, lo, nf, k, F.p.p,
+                                                                       F.u.p, F.f_off.p, ws, perturbed);
                 MWI_CHECK_LAUNCH();
-                MWI_REQUIRE(range + 1 < ut.ptr.size(), MWI_EINVAL, "internal: update tile list out of step");
+                {
+                    const int64_t r0 = ut.rptr[range], r1 = ut.rptr[range + 1];
+                    if (r1 > r0) {
+                        panel_rows_kernel<C, NB><<<(unsigned)(r1 - r0), 128, 0, st>>>(ut.rtiles.p + r0, k, F.p.p,
+                                                                                     F.u.p, F.f_off.p, ws);
+                        MWI_CHECK_LAUNCH();
+                    }
+                }
+                MWI_REQUIRE(range + 1 < ut.ptr.size() && range + 1 < ut.rptr.size(), MWI_EINVAL,
+                            "internal: update tile list out of step");
                 const int64_t t0 = ut.ptr[range], t1 = ut.ptr[range + 1];
                 ++range;
                 if (t1 > t0) {

@@ -119,6 +119,9 @@ struct UpdateTiles {
     int nb = 0, tile = 0;
     DevBuf<int4> tiles;
     std::vector<int64_t> ptr;
+    // panel-row tiles (front, first row) of 128 rows below each step's diagonal block
+    DevBuf<int2> rtiles;
+    std::vector<int64_t> rptr;
 };
 int factor_block_cols(bool fp32);
 int factor_tile_rows(bool fp32);
