@@ -18,7 +18,9 @@ What it computes, in complex128, by the plain definitions:
 * the one-level ORAS preconditioner (Eq. ORAS) with the partition of unity of
   Section 3.2 (Eq. algebPartUnity, Eq. chi) and a right-preconditioned
   flexible GMRES, used where a direct solve is too large and to check the
-  preconditioner's pieces one by one (``dd``).
+  preconditioner's pieces one by one (``dd``);
+* the nodal (P1) permittivity parameter with the gradient penalty and the
+  normalised misfit weights of Eq. defJ2 (``p1``).
 
 Parity status: every function is pinned by the tests under ``tests/`` that run
 with ``-m "not gpu"`` (closed forms, the discrete curl-grad identity, symmetry,
@@ -40,9 +42,10 @@ from .solve import (
     misfit_and_gradient,
 )
 from . import dd
+from . import p1
 
 __all__ = [
     "C0", "MU0", "k0_of", "Topology", "build_topology", "element_matrices", "face_matrix",
     "basis_at", "assemble_system", "antenna_edges", "build_rhs", "direct_solve", "s_matrix",
-    "misfit", "adjoint_rhs", "gradient", "forward", "misfit_and_gradient", "dd",
+    "misfit", "adjoint_rhs", "gradient", "forward", "misfit_and_gradient", "dd", "p1",
 ]
