@@ -220,6 +220,27 @@ def run_mine(args, rank, world):
     results["mixed"] = one_arm(1, args.steps, args.warmup, max(2, args.requests))
     results["nested"] = one_arm(2, args.nested_steps, args.warmup, 0) if args.nested_steps > 0 else None
     results["fp64"] = one_arm(0, args.fp64_steps, args.warmup, 0) if args.fp64_steps > 0 else None
+    # nodal (P1) parameter with the gradient penalty: the two kernels a P1
+    # objective adds to a gradient step (centroid sampling, spreading + penalty)
+    with torch.cuda.stream(stream):
+        kap = torch.full((mesh.nv,), 44 - 20j, dtype=torch.complex128, device=dev)
+        kap += torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, mesh.nv)).to(dev)
+        g_t = torch.from_numpy(np.random.default_rng(4).standard_normal(mesh.nt) + 0j).to(dev)
+        for _ in range(3):
+            M.p1_tet_eps(kap, stream)
+            M.p1_gradient(g_t, kap, 1e-3, stream)
+        reps = 50
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for _ in range(reps):
+            M.p1_tet_eps(kap, stream)
+        e1.record(stream)
+        for _ in range(reps):
+            M.p1_gradient(g_t, kap, 1e-3, stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        results["p1"] = {"tet_eps_ms": e0.elapsed_time(e1) / reps, "gradient_and_penalty_ms": e1.elapsed_time(e2) / reps,
+                         "nv": int(mesh.nv), "what": "per call, including the penalty read-back to the host"}
     return mesh, M, results
 
 
@@ -340,6 +361,8 @@ def main():
         "kernel_ms_per_step": {k: round(v / mx["steps"], 3) for k, v in
                                zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"], mx["kernel_ms"])},
         "solver": {"fwd": mx["fwd_info"], "adj": mx["adj_info"], "factor": mx["factor"]},
+        "next_rows": {"p1_parameter": {k: (round(v, 4) if isinstance(v, float) else v)
+                                       for k, v in R["p1"].items()}} if R.get("p1") else None,
     }
     if R["fp64"]:
         f = R["fp64"]

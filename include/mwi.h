@@ -245,6 +245,26 @@ mwi_status mwi_decomposition(mwi_problem_t prob, int32_t* part, int64_t* n_local
 mwi_status mwi_factor_stats(mwi_problem_t prob, int64_t* factor_entries, int64_t* n_fronts,
                             int64_t* max_front, double* factor_flops);
 
+/* Nodal (P1) permittivity parameter (the P1 parameter of Section 6.3).
+ * Per-tet relative permittivity from per-vertex values kappa_dev [nv] (complex,
+ * interleaved; the caller's vertex numbering): eps_t = (1/4) sum of kappa over
+ * the tet's vertices, i.e. the P1 field at the tet's centroid, written to
+ * eps_dev [nt] (device, the layout mwi_update_eps_device reads).  Enqueued on
+ * `stream`; no synchronisation. */
+mwi_status mwi_p1_tet_eps(mwi_mesh_t mesh, const double* kappa_dev, double* eps_dev, void* stream);
+
+/* Gradient of Phi(kappa) = J(eps(kappa)) + R(kappa) with respect to the nodal
+ * parameter, R = (alpha/2) integral |grad kappa|^2 = (alpha/2) Re(kappa^H K kappa)
+ * (the gradient penalty of Eq. defJ2; K the P1 stiffness matrix of the mesh,
+ * built on the first call).  grad_tet_dev [nt]: the per-tet gradient of J as
+ * mwi_misfit_and_gradient_device returns it (dJ/dRe eps_t + i dJ/dIm eps_t);
+ * grad_vertex_dev [nv] receives 1/4 sum over the vertex's tets of grad_tet plus
+ * alpha (K kappa)_v, in the same convention.  penalty (host, may be NULL): R;
+ * when given, the call synchronises `stream`.  Errors: MWI_EINVAL for null
+ * pointers or alpha < 0. */
+mwi_status mwi_p1_gradient(mwi_mesh_t mesh, const double* grad_tet_dev, const double* kappa_dev, double alpha,
+                           double* grad_vertex_dev, double* penalty, void* stream);
+
 /* Algorithmic memory traffic of one ORAS application (Eq. ORAS) to m columns,
  * in bytes, for the roofline of the sweeps (no counterpart in the paper; a
  * measurement aid): every stored factor entry read once per sweep (the unit

@@ -96,6 +96,11 @@ struct mwi_mesh {
     DevBuf<int32_t> A_fu_face, A_fu_tet;
     std::vector<std::shared_ptr<DecompEntry>> cache;
     std::mutex mu;
+    // nodal (P1) parameter: vertex -> tets, P1 stiffness, block partial sums (built on first use)
+    bool have_p1 = false;
+    DevBuf<int32_t> v2t_ptr, v2t, p1_rp, p1_col;
+    DevBuf<double> p1_val, p1_partial;
+    std::vector<double> p1_partial_host;
 };
 
 struct mwi_problem {
@@ -1114,6 +1119,55 @@ mwi_status mwi_factor_stats(mwi_problem_t P, int64_t* factor_entries, int64_t* n
         if (n_fronts) *n_fronts = (int64_t)D.fronts.size();
         if (max_front) *max_front = D.max_front;
         if (factor_flops) *factor_flops = D.factor_flops;
+    });
+}
+
+static void ensure_p1(mwi_mesh* M) {
+    std::lock_guard<std::mutex> lk(M->mu);
+    if (M->have_p1) return;
+    const Topology& T = M->T;
+    std::vector<int32_t> rp, col;
+    std::vector<double> val;
+    build_p1_stiffness(T, rp, col, val);
+    up(M->v2t_ptr, T.v2t_ptr, M->st);
+    up(M->v2t, T.v2t, M->st);
+    up(M->p1_rp, rp, M->st);
+    up(M->p1_col, col, M->st);
+    up(M->p1_val, val, M->st);
+    M->p1_partial.alloc((size_t)p1_gradient_blocks(T.nv));
+    M->p1_partial_host.assign((size_t)p1_gradient_blocks(T.nv), 0.0);
+    MWI_CUDA(cudaStreamSynchronize(M->st));
+    M->have_p1 = true;
+}
+
+mwi_status mwi_p1_tet_eps(mwi_mesh_t M, const double* kappa_dev, double* eps_dev, void* stream) {
+    return guard([&] {
+        MWI_REQUIRE(M && kappa_dev && eps_dev, MWI_EINVAL, "null argument");
+        launch_p1_tet_eps(M->T.nt, M->tv.p, (const double2*)kappa_dev, (double2*)eps_dev, (cudaStream_t)stream);
+    });
+}
+
+mwi_status mwi_p1_gradient(mwi_mesh_t M, const double* grad_tet_dev, const double* kappa_dev, double alpha,
+                           double* grad_vertex_dev, double* penalty, void* stream) {
+    return guard([&] {
+        MWI_REQUIRE(M && grad_tet_dev && kappa_dev && grad_vertex_dev, MWI_EINVAL, "null argument");
+        MWI_REQUIRE(alpha >= 0.0 && std::isfinite(alpha), MWI_EINVAL, "alpha must be finite and >= 0");
+        ensure_p1(M);
+        cudaStream_t st = (cudaStream_t)stream;
+        const int64_t nv = M->T.nv;
+        launch_p1_gradient(nv, M->v2t_ptr.p, M->v2t.p, (const double2*)grad_tet_dev, M->p1_rp.p, M->p1_col.p,
+                           M->p1_val.p, (const double2*)kappa_dev, alpha, (double2*)grad_vertex_dev,
+                           M->p1_partial.p, st);
+        if (penalty) {
+            std::lock_guard<std::mutex> lk(M->mu);
+            const size_t nb = M->p1_partial_host.size();
+            MWI_CUDA(cudaMemcpyAsync(M->p1_partial_host.data(), M->p1_partial.p, nb * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
+            MWI_CUDA(cudaStreamSynchronize(st));
+            double sum = 0.0;
+            for (size_t b = 0; b < nb; ++b) sum += M->p1_partial_host[b];
+            *penalty = 0.5 * alpha * sum;
+        }
     });
 }
 

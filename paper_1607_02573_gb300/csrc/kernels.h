@@ -148,6 +148,16 @@ size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed);
 void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const double2* x, double2* y, int m,
                         int64_t n, cudaStream_t st, int tc = 0);
 
+// ---- nodal (P1) permittivity parameter (p1.cu)
+struct Topology;
+void build_p1_stiffness(const Topology& T, std::vector<int32_t>& rp, std::vector<int32_t>& col,
+                        std::vector<double>& val);
+void launch_p1_tet_eps(int64_t nt, const int32_t* tv, const double2* kappa, double2* eps, cudaStream_t st);
+int p1_gradient_blocks(int64_t nv);
+void launch_p1_gradient(int64_t nv, const int32_t* v2t_ptr, const int32_t* v2t, const double2* grad_t,
+                        const int32_t* rp, const int32_t* col, const double* val, const double2* kappa, double alpha,
+                        double2* out, double* partial, cudaStream_t st);
+
 // ---- Krylov building blocks (krylov.cu)
 template <typename C>
 void spmm(int64_t n, const int32_t* row_ptr, const int32_t* col, const C* val, const C* x, C* y, int m,

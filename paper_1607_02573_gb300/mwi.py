@@ -77,6 +77,8 @@ _SIGS = {
     "mwi_decomposition": [_vp, _i32p, _i64p],
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
     "mwi_oras_traffic": [_vp, C.c_int32, _dp],
+    "mwi_p1_tet_eps": [_vp, _vp, _vp, _vp],
+    "mwi_p1_gradient": [_vp, _vp, _vp, C.c_double, _vp, _dp, _vp],
     "mwi_kernel_times": [_vp, _dp, _i64p, C.c_int32],
     "mwi_misfit": [_vp, _dp, _dp, _dp],
 }
@@ -144,6 +146,29 @@ class Mesh:
         n = C.c_int64()
         check(mwi_mesh_ndof(h, C.byref(n)))
         self.ndof = n.value
+
+    def p1_tet_eps(self, kappa, stream=None):
+        """Per-tet permittivity (device tensor [nt]) from per-vertex values kappa (device tensor [nv])."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        k = kappa.to(torch.complex128).contiguous()
+        eps = torch.empty(self.nt, dtype=torch.complex128, device=k.device)
+        check(mwi_p1_tet_eps(self.h, _vp(k.data_ptr()), _vp(eps.data_ptr()), _vp(stream.cuda_stream)))
+        return eps
+
+    def p1_gradient(self, grad_tet, kappa, alpha, stream=None):
+        """Per-vertex gradient (device tensor [nv]) of J(eps(kappa)) + R(kappa) and the penalty R."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        g = grad_tet.to(torch.complex128).contiguous()
+        k = kappa.to(torch.complex128).contiguous()
+        out = torch.empty_like(k)
+        R = C.c_double()
+        check(mwi_p1_gradient(self.h, _vp(g.data_ptr()), _vp(k.data_ptr()), float(alpha), _vp(out.data_ptr()),
+                              C.byref(R), _vp(stream.cuda_stream)))
+        return out, R.value
 
     def dof_keys(self):
         kind = np.empty(self.ndof, dtype=np.int32)
@@ -219,6 +244,23 @@ class Problem:
         info = mwi_solve_info()
         st = mwi_misfit_and_gradient(self.h, _ptr(Sm.view(np.float64), C.c_double), wp, C.byref(J),
                                      _ptr(grad.view(np.float64), C.c_double), C.byref(info))
+        check(st, allow=(MWI_ENOTCONV,) if allow_notconv else ())
+        self.info = info
+        return J.value, grad
+
+    def misfit_and_gradient_device(self, S_meas, w=None, allow_notconv=False):
+        """J and the per-tet gradient as a device tensor [nt] (measurements and weights from host arrays)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Sm = torch.from_numpy(np.ascontiguousarray(np.asarray(S_meas, dtype=np.complex128).T)).to(dev)
+        wd = None
+        if w is not None:
+            wd = torch.from_numpy(np.ascontiguousarray(np.asarray(w, dtype=np.float64).T)).to(dev)
+        grad = torch.empty(self.mesh.nt, dtype=torch.complex128, device=dev)
+        J = C.c_double()
+        info = mwi_solve_info()
+        st = mwi_misfit_and_gradient_device(self.h, _vp(Sm.data_ptr()), _vp(wd.data_ptr()) if wd is not None else None,
+                                            C.byref(J), _vp(grad.data_ptr()), C.byref(info))
         check(st, allow=(MWI_ENOTCONV,) if allow_notconv else ())
         self.info = info
         return J.value, grad
