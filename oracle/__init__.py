@@ -20,7 +20,9 @@ What it computes, in complex128, by the plain definitions:
   flexible GMRES, used where a direct solve is too large and to check the
   preconditioner's pieces one by one (``dd``);
 * the nodal (P1) permittivity parameter with the gradient penalty and the
-  normalised misfit weights of Eq. defJ2 (``p1``).
+  normalised misfit weights of Eq. defJ2 (``p1``);
+* block flexible GMRES, one Krylov space shared by the right-hand sides of a
+  block (the block methods of Section 7) (``block_gmres``).
 
 Parity status: every function is pinned by the tests under ``tests/`` that run
 with ``-m "not gpu"`` (closed forms, the discrete curl-grad identity, symmetry,
@@ -43,9 +45,11 @@ from .solve import (
 )
 from . import dd
 from . import p1
+from . import block_gmres
 
 __all__ = [
     "C0", "MU0", "k0_of", "Topology", "build_topology", "element_matrices", "face_matrix",
     "basis_at", "assemble_system", "antenna_edges", "build_rhs", "direct_solve", "s_matrix",
     "misfit", "adjoint_rhs", "gradient", "forward", "misfit_and_gradient", "dd", "p1",
+    "block_gmres",
 ]

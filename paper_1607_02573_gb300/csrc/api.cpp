@@ -407,6 +407,16 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
                 for (int r = 0; r < fr.p; r += TL.tm) { d.row0 = r; pt.push_back(d); }
                 for (int r = 0; r < fr.p + fr.u; r += TL.tm) { d.row0 = r; ft.push_back(d); }
             }
+            // heaviest tiles first within a level (longest-processing-time
+            // order), so the last wave is not left with the longest tiles;
+            // the tiles of one level are independent, so the order is free
+            const int tm = TL.tm;
+            std::stable_sort(pt.begin() + TL.p_ptr.back(), pt.end(), [](const TileDesc& a, const TileDesc& b) {
+                return a.f - a.row0 > b.f - b.row0;
+            });
+            std::stable_sort(ft.begin() + TL.f_ptr.back(), ft.end(), [tm](const TileDesc& a, const TileDesc& b) {
+                return std::min(a.p, a.row0 + tm) > std::min(b.p, b.row0 + tm);
+            });
             TL.p_ptr.push_back((int64_t)pt.size());
             TL.f_ptr.push_back((int64_t)ft.size());
         }
