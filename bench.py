@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--n-ant", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nd-leaf", type=int, default=64)
+    ap.add_argument("--block-steps", type=int, default=1,
+                    help="timed forward solves comparing true block FGMRES with pseudo-block (0: skip)")
     ap.add_argument("--engine", type=int, default=2, help="complex FP32 sweep engine (see mwi_solver_opts)")
     ap.add_argument("--requests", type=int, default=200,
                     help="end-to-end gradient requests (host in, host out) for e2e throughput and p50/p99 latency")
@@ -220,6 +222,32 @@ def run_mine(args, rank, world):
     results["mixed"] = one_arm(1, args.steps, args.warmup, max(2, args.requests))
     results["nested"] = one_arm(2, args.nested_steps, args.warmup, 0) if args.nested_steps > 0 else None
     results["fp64"] = one_arm(0, args.fp64_steps, args.warmup, 0) if args.fp64_steps > 0 else None
+    # true block FGMRES (one Krylov space for the 32 columns) against the
+    # pseudo-block FGMRES on the same forward solve of the 32 transmitters
+    if args.block_steps > 0:
+        results["block"] = {}
+        for name, bk in (("pseudo_block", 0), ("block", 1)):
+            P = mwi.Problem(M, eps_d, FREQ, stream=stream, n_sub=64, precision=1, rtol=RTOL, verbose=2,
+                            max_iter=500, nd_leaf=args.nd_leaf, sweep_engine=args.engine, block_krylov=bk)
+            P.forward_solve(ants, ants)
+            P.kernel_times(reset=True)
+            torch.cuda.synchronize()
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            for _ in range(args.block_steps):
+                P.forward_solve(ants, ants)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fms = e0.elapsed_time(e1) / args.block_steps
+            kms, _ = P.kernel_times(reset=True)
+            info = P.info.as_dict()
+            results["block"][name] = {
+                "iterations": info["iters_max"], "forward_ms": round(fms, 2),
+                "rhs_solves_per_s": round(ants.shape[0] / (fms / 1e3), 2), "resid_max": info["resid_max"],
+                "converged": info["n_converged"],
+                "kernel_ms": {k: round(v / args.block_steps, 2) for k, v in
+                              zip(["spmm", "oras_apply", "orthogonalisation"], kms[:3].tolist())}}
+            P.close()
     # nodal (P1) parameter with the gradient penalty: the two kernels a P1
     # objective adds to a gradient step (centroid sampling, spreading + penalty)
     with torch.cuda.stream(stream):
@@ -362,7 +390,11 @@ def main():
                                zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"], mx["kernel_ms"])},
         "solver": {"fwd": mx["fwd_info"], "adj": mx["adj_info"], "factor": mx["factor"]},
         "next_rows": {"p1_parameter": {k: (round(v, 4) if isinstance(v, float) else v)
-                                       for k, v in R["p1"].items()}} if R.get("p1") else None,
+                                       for k, v in R["p1"].items()} if R.get("p1") else None,
+                      "block_fgmres": dict(R["block"], what="forward solve of the 32 transmitters, FP32 ORAS "
+                                           "preconditioner; block: one shared Krylov space, FP64 block vectors; "
+                                           "pseudo_block: the double-float per-column FGMRES of the main line")
+                      if R.get("block") else None},
     }
     if R["fp64"]:
         f = R["fp64"]

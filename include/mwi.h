@@ -97,6 +97,15 @@ typedef struct {
                              parts (about FP32 accuracy); 2 = tensor cores, plain TF32 (the
                              preconditioner carries ~1e-3 relative rounding, absorbed by the
                              outer FGMRES); 3 = CUDA cores, FP32 */
+    int32_t block_krylov; /* 0 = pseudo-block FGMRES: every column of a block keeps its own
+                             Krylov space and the columns' operations are fused (Section 6.3)
+                             [0]; 1 = true block FGMRES (the block methods of Section 7): one
+                             Krylov space shared by the columns of a block, built by block
+                             Arnoldi with block classical Gram-Schmidt (twice) and Cholesky QR
+                             (twice), complex FP64 vectors, blocks of at most 32 columns (a
+                             column whose new direction falls below 1e-7 of its norm is
+                             deflated); the preconditioner is the ORAS of `precision`.
+                             iters_max then counts block steps.  Other values: MWI_EINVAL */
 } mwi_solver_opts;
 
 typedef struct {

@@ -121,6 +121,7 @@ struct mwi_problem {
     Gmres<double2> outer;
     Gmres<float2> inner;
     GmresDF dfk;                         // MIXED: double-float FGMRES
+    BlockGmres bgm;                      // true block FGMRES (block_krylov = 1)
     DevBuf<float2> Adf, Bdf, Xdf, Rdf;   // double-float planes
     DevBuf<double2> U, Lam, Brhs, R, Bc, Xc;
     DevBuf<float2> v32, x32, r32;
@@ -191,6 +192,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     if (d.nd_leaf <= 0) d.nd_leaf = 64;
     if (d.max_block <= 0) d.max_block = 64;
     if (d.sweep_engine <= 0) d.sweep_engine = 2;
+    if (d.block_krylov < 0 || d.block_krylov > 1) throw Error(MWI_EINVAL, "block_krylov must be 0 or 1");
     return d;
 }
 
@@ -578,10 +580,71 @@ void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<in
 void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info);
 void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info);
 
+// True block FGMRES (one Krylov space for the m columns) with FP64 vectors;
+// the preconditioner M64 is the ORAS of the problem's precision
+void solve_block_krylov(mwi_problem* P, const OpFnT<double2>& A64, const OpFnT<double2>& M64, const double2* B,
+                        double2* X, int m, int restart, double t0, mwi_solve_info* info) {
+    const int64_t n = P->mesh->T.ndof;
+    const int64_t nm = n * m;
+    cudaStream_t st = P->st;
+    const mwi_solver_opts& o = P->opts;
+    BlockGmres& G = P->bgm;
+    G.reserve(n, m, restart);
+    G.timer = [P](int slot, const std::function<void()>& fn) { timed(P, slot, fn); };
+    P->R.ensure(nm);
+    std::vector<double2> gram((size_t)m * m);
+    auto col_norms = [&](const double2* x, std::vector<double>& out) {
+        G.block_dots(x, 1, x, G.small.p, st);
+        MWI_CUDA(cudaMemcpyAsync(gram.data(), G.small.p, gram.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+        out.resize(m);
+        for (int c = 0; c < m; ++c) out[c] = std::sqrt(std::max(gram[(size_t)c * m + c].x, 0.0));
+    };
+    std::vector<double> bn, rn, tol(m), est(m);
+    col_norms(B, bn);
+    for (int c = 0; c < m; ++c) tol[c] = o.rtol * bn[c];
+    MWI_CUDA(cudaMemsetAsync(X, 0, nm * sizeof(double2), st));
+    MWI_CUDA(cudaMemcpyAsync(P->R.p, B, nm * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    rn = bn;
+    int total = 0, deflated = 0;
+    while (true) {
+        int defl = 0;
+        const int used = G.cycle(A64, M64, P->R.p, X, tol, std::min(restart, o.max_iter - total), st, est.data(), &defl);
+        total += used;
+        deflated += defl;
+        A64(X, P->R.p);
+        residual_c128(nm, B, P->R.p, st);
+        col_norms(P->R.p, rn);
+        bool done = true;
+        for (int c = 0; c < m; ++c)
+            if (bn[c] > 0 && rn[c] > o.rtol * bn[c]) done = false;
+        if (done || total >= o.max_iter || used == 0) break;
+    }
+    int nconv = 0;
+    double rmax = 0;
+    for (int c = 0; c < m; ++c) {
+        const double rel = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+        rmax = std::max(rmax, rel);
+        if (rel <= o.rtol) nconv++;
+    }
+    if (o.verbose) std::fprintf(stderr, "[mwi] block FGMRES: %d steps, %d deflated columns\n", total, deflated);
+    if (info) {
+        info->iters_max = total;
+        info->inner_total = P->inner_total;
+        info->n_converged = nconv;
+        info->n_perturbed = P->n_perturbed;
+        info->resid_max = rmax;
+        info->setup_ms = P->setup_ms;
+        info->solve_ms = now_ms() - t0;
+    }
+    if (nconv < m) throw Error(MWI_ENOTCONV, "block FGMRES did not reach rtol on every column");
+}
+
 // solve A X = B for m columns in blocks of at most opts.max_block columns
 // (Krylov bases scale with the block width); X and B are [n][m]
 void solve_columns(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
-    const int mb = P->opts.max_block;
+    // a shared block Krylov space costs m^2 per row in its Gram-Schmidt: at most 32 columns
+    const int mb = P->opts.block_krylov ? std::min(P->opts.max_block, 32) : P->opts.max_block;
     if (m <= mb) {
         solve_block(P, B, X, m, info);
         return;
@@ -626,14 +689,15 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     const mwi_solver_opts& o = P->opts;
     const bool mixed = o.precision != 0;
     const bool nested = o.precision == 2;
-    if (mixed && !nested) {
+    const bool block = o.block_krylov != 0;
+    if (mixed && !nested && !block) {
         solve_block_df(P, B, X, m, info);
         return;
     }
     DecompEntry& E = *P->dec;
     // with an inner GMRES the outer FGMRES needs few steps: keep its FP64 bases short
     const int restart = std::min(nested ? std::min(o.restart, 12) : o.restart, std::max(1, o.max_iter));
-    P->outer.reserve(n, m, restart);
+    if (!block) P->outer.reserve(n, m, restart);
     P->R.ensure(nm);
     P->dscratch.ensure(4 * (size_t)m);
     double* b2 = P->dscratch.p;
@@ -697,6 +761,10 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     P->inner.timer = tfn;
     const double t0 = now_ms();
     P->inner_total = 0;
+    if (block) {
+        solve_block_krylov(P, A64, M64, B, X, m, restart, t0, info);
+        return;
+    }
     P->outer.column_norms2(B, b2, st);
     tolerances(m, b2, o.rtol, tol, bnorm, st);
     std::vector<double> bn(m), rn(m);

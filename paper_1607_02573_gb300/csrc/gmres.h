@@ -1,7 +1,9 @@
 // Pseudo-block flexible GMRES engine over row-major [n][m] device vectors.
 #pragma once
 
+#include <complex>
 #include <functional>
+#include <vector>
 
 #include "common.h"
 
@@ -68,6 +70,28 @@ struct GmresDF {
               cudaStream_t st, int* iters_used);
     // ||x_c||^2 from the FP32 head plane
     void norms2(const float2* xh, double* out, cudaStream_t st);
+};
+
+// True block flexible GMRES over complex FP64 [n][m] blocks: one Krylov space
+// shared by the m <= 32 columns (block Arnoldi, block classical Gram-Schmidt
+// twice, Cholesky QR twice, Givens QR of the block Hessenberg on the host).
+struct BlockGmres {
+    int64_t n = 0;
+    int m = 0, restart = 0;
+    DevBuf<double2> V, Z, W, coef, small, partial;
+    std::function<void(int, const std::function<void()>&)> timer;
+
+    void reserve(int64_t n, int m, int restart);
+    // One cycle from the residual r0 (x updated in place): at most max_steps
+    // block steps, stopping when every column's least-squares residual is
+    // <= tol[c] (absolute).  resid_est (host, m) gets the last estimates and
+    // deflated the number of columns dropped by the Cholesky QRs.  Returns steps.
+    int cycle(const OpFnT<double2>& A, const OpFnT<double2>& M, const double2* r0, double2* x,
+              const std::vector<double>& tol, int max_steps, cudaStream_t st, double* resid_est, int* deflated);
+    void block_dots(const double2* V, int nq, const double2* W, double2* out, cudaStream_t st);
+    void block_update(double2* out, const double2* in, int nq, const double2* Cm, double alpha, double beta,
+                      cudaStream_t st);
+    int chol_qr(double2* X, std::vector<std::complex<double>>& S, cudaStream_t st);
 };
 
 // w = A z with A as double-float planes (hi nnz entries, then lo), z complex FP32

@@ -37,7 +37,8 @@ class mwi_solver_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("restart", C.c_int32), ("n_sub", C.c_int32),
                 ("overlap", C.c_int32), ("precision", C.c_int32), ("inner_iters", C.c_int32),
                 ("inner_rtol", C.c_double), ("nd_leaf", C.c_int32), ("verbose", C.c_int32),
-                ("part", C.POINTER(C.c_int32)), ("max_block", C.c_int32), ("sweep_engine", C.c_int32)]
+                ("part", C.POINTER(C.c_int32)), ("max_block", C.c_int32), ("sweep_engine", C.c_int32),
+                ("block_krylov", C.c_int32)]
 
 
 class mwi_solve_info(C.Structure):
@@ -121,7 +122,10 @@ def _antennas(arr):
 def make_opts(**kw):
     o = mwi_solver_opts()
     part = kw.pop("part", None)
+    names = {f for f, _ in mwi_solver_opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown solver option {k!r}")
         setattr(o, k, v)
     keep = None
     if part is not None:
