@@ -23,10 +23,15 @@ residual on any column than single-vector GMRES after the same number of steps.
 The least-squares problem is solved here with a library least-squares routine
 on the whole Hbar_k, not with the rotations a production solver updates.
 
+It also states the initial guess taken from a recycled subspace (the previous
+system's solutions), the recycling Section 7 cites.
+
 Parity status: pinned by tests/test_oracle_block_gmres.py (the iterate equals
 the least-residual element of the explicitly built block Krylov space, column
 by column; exact solution once the space is the whole space; no column worse
-than single-vector GMRES at the same step).
+than single-vector GMRES at the same step; the recycled initial guess leaves a
+residual orthogonal to A span(Xprev), beats every other element of the span
+tried, and is exact when Xprev holds the solution).
 """
 
 import numpy as np
@@ -120,3 +125,13 @@ def krylov_basis(A, M, R0, k, block=True):
             p = w / np.linalg.norm(w)
         out.append(np.hstack(cols))
     return out
+
+
+def recycled_initial_guess(A, B, Xprev):
+    """Initial guess from a recycled subspace (the recycling of Section 7,
+    Parks et al.): column by column the element of span(Xprev) with the least
+    residual, x0_c = Xprev y_c with y_c = argmin ||b_c - A Xprev y||.  Xprev is
+    the solution block of a previous, nearby system (the previous L-BFGS step)."""
+    AX = _apply(A, np.asarray(Xprev, dtype=np.complex128))
+    Y = np.linalg.lstsq(AX, np.asarray(B, dtype=np.complex128), rcond=None)[0]
+    return np.asarray(Xprev, dtype=np.complex128) @ Y

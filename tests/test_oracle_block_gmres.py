@@ -8,7 +8,10 @@ compared with the pseudo-block GMRES of Section 6.3).
   its own space M K_k(A M, r_0c) (that space is contained in the block one);
 * once k m reaches n the space is everything and the solve is exact;
 * on the chamber system with the ORAS preconditioner, the block solve reaches
-  the direct solution in no more steps than the column-by-column FGMRES.
+  the direct solution in no more steps than the column-by-column FGMRES;
+* the initial guess from a recycled subspace (Section 7's recycling) leaves a
+  residual orthogonal to A span(Xprev), no other element of the span does
+  better, and recycling the exact solutions gives them back.
 """
 
 import numpy as np
@@ -75,3 +78,22 @@ def test_chamber_with_oras_reaches_direct_solution():
     assert np.linalg.norm(U - X, axis=0).max() <= 1e-8 * np.linalg.norm(U, axis=0).min()
     singles = [dd.fgmres(A, B[:, c], oras.apply, rtol=1e-10)[1] for c in range(B.shape[1])]
     assert steps <= max(singles)
+
+
+def test_recycled_initial_guess_is_least_residual_in_span():
+    A, B, P = _system(50, 4, 4)
+    rng = np.random.default_rng(5)
+    Xprev = np.linalg.solve(A + 0.05 * np.eye(50), B) + 0.01 * rng.standard_normal((50, 4))
+    x0 = bg.recycled_initial_guess(A, B, Xprev)
+    R = B - A @ x0
+    AX = A @ Xprev
+    # residual orthogonal to A span(Xprev), so no other element of the span does better
+    assert np.abs(AX.conj().T @ R).max() <= 1e-10 * np.abs(AX).max() * np.abs(B).max()
+    for _ in range(5):
+        other = x0 + Xprev @ (1e-3 * (rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))))
+        assert np.all(np.linalg.norm(B - A @ other, axis=0) >= np.linalg.norm(R, axis=0) * (1 - 1e-12))
+    # recycling the exact solutions reproduces them
+    X = np.linalg.solve(A, B)
+    assert np.linalg.norm(bg.recycled_initial_guess(A, B, X) - X) <= 1e-10 * np.linalg.norm(X)
+    # a nearby system's solutions already cut the residual
+    assert np.linalg.norm(R) < 0.2 * np.linalg.norm(B)
