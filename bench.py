@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--n-ant", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nd-leaf", type=int, default=64)
+    ap.add_argument("--recycle-steps", type=int, default=3,
+                    help="timed gradient steps with Krylov recycling across steps (0: skip)")
     ap.add_argument("--block-steps", type=int, default=1,
                     help="timed forward solves comparing true block FGMRES with pseudo-block (0: skip)")
     ap.add_argument("--engine", type=int, default=2, help="complex FP32 sweep engine (see mwi_solver_opts)")
@@ -140,9 +142,9 @@ def run_mine(args, rank, world):
     eps_d = torch.from_numpy(eps).to(dev)
     results = {}
 
-    def one_arm(precision, steps, warmup, e2e_steps):
+    def one_arm(precision, steps, warmup, e2e_steps, recycle=0):
         P = mwi.Problem(M, eps_d, FREQ, stream=stream, n_sub=64, precision=precision, rtol=RTOL,
-                        verbose=2, max_iter=500, nd_leaf=args.nd_leaf, sweep_engine=args.engine)
+                        verbose=2, max_iter=500, nd_leaf=args.nd_leaf, sweep_engine=args.engine, recycle=recycle)
         fs = P.factor_stats()
         fs["oras_bytes_per_call"] = P.oras_traffic(min(32, args.n_ant))
         # synthetic measurements: S of the two-inclusion target map plus 1 % noise
@@ -222,6 +224,9 @@ def run_mine(args, rank, world):
     results["mixed"] = one_arm(1, args.steps, args.warmup, max(2, args.requests))
     results["nested"] = one_arm(2, args.nested_steps, args.warmup, 0) if args.nested_steps > 0 else None
     results["fp64"] = one_arm(0, args.fp64_steps, args.warmup, 0) if args.fp64_steps > 0 else None
+    # Krylov recycling: the same step sequence (eps_r alternating between two maps 1 % apart, as
+    # consecutive L-BFGS steps), every solve starting from the previous step's solution span
+    results["recycle"] = one_arm(1, args.recycle_steps, args.warmup, 0, recycle=1) if args.recycle_steps > 0 else None
     # true block FGMRES (one Krylov space for the 32 columns) against the
     # pseudo-block FGMRES on the same forward solve of the 32 transmitters
     if args.block_steps > 0:
@@ -394,7 +399,20 @@ def main():
                       "block_fgmres": dict(R["block"], what="forward solve of the 32 transmitters, FP32 ORAS "
                                            "preconditioner; block: one shared Krylov space, FP64 block vectors; "
                                            "pseudo_block: the double-float per-column FGMRES of the main line")
-                      if R.get("block") else None},
+                      if R.get("block") else None,
+                      "krylov_recycling": {
+                          "value": round(R["recycle"]["value"], 3), "unit": UNIT,
+                          "ms_per_step": round(R["recycle"]["ms_per_step"], 2), "steps": R["recycle"]["steps"],
+                          "fwd_iterations": R["recycle"]["fwd_info"]["iters_max"],
+                          "adj_iterations": R["recycle"]["adj_info"]["iters_max"],
+                          "converged_columns": R["recycle"]["converged"],
+                          "expected_columns": R["recycle"]["expected"],
+                          "kernel_ms_per_step": {k: round(v / R["recycle"]["steps"], 3) for k, v in
+                                                 zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"],
+                                                     R["recycle"]["kernel_ms"])},
+                          "what": "the main line's gradient steps with recycle = 1: each forward (adjoint) "
+                                  "solve starts from the least-residual element of the previous step's "
+                                  "forward (adjoint) solution span"} if R.get("recycle") else None},
     }
     if R["fp64"]:
         f = R["fp64"]

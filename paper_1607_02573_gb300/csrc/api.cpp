@@ -122,6 +122,11 @@ struct mwi_problem {
     Gmres<float2> inner;
     GmresDF dfk;                         // MIXED: double-float FGMRES
     BlockGmres bgm;                      // true block FGMRES (block_krylov = 1)
+    // recycling: columns of the resident forward (0) / adjoint (1) solution usable
+    // as the recycled space of the next solve (0 = none)
+    int rec_m[2] = {0, 0};
+    int rec_dropped = 0;
+    DevBuf<double2> rc_scratch;
     DevBuf<float2> Adf, Bdf, Xdf, Rdf;   // double-float planes
     DevBuf<double2> U, Lam, Brhs, R, Bc, Xc;
     DevBuf<float2> v32, x32, r32;
@@ -193,6 +198,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     if (d.max_block <= 0) d.max_block = 64;
     if (d.sweep_engine <= 0) d.sweep_engine = 2;
     if (d.block_krylov < 0 || d.block_krylov > 1) throw Error(MWI_EINVAL, "block_krylov must be 0 or 1");
+    if (d.recycle < 0 || d.recycle > 1) throw Error(MWI_EINVAL, "recycle must be 0 or 1");
     return d;
 }
 
@@ -577,13 +583,46 @@ void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<in
 }
 
 // solve A X = B for m columns by FGMRES; returns info
-void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info);
-void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info);
+// x0: X holds an initial guess (else the solve starts from zero)
+void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info, bool x0 = false);
+void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info, bool x0);
+
+// On entry X holds the previous system's solution block (m <= 32 columns); on
+// exit the least-residual element of its span for every column of B (the
+// recycled initial guess, in FP32 arithmetic)
+void recycle_guess(mwi_problem* P, const double2* B, double2* X, int m) {
+    mwi_mesh* M = P->mesh;
+    const int64_t n = M->T.ndof;
+    const int64_t nm = n * m;
+    cudaStream_t st = P->st;
+    P->v32.ensure(nm);
+    P->x32.ensure(nm);
+    P->r32.ensure(nm);
+    P->rc_scratch.ensure(recycle_scratch_entries(m));
+    convert_c128_to_c64(nm, X, P->v32.p, st);
+    convert_c128_to_c64(nm, B, P->r32.p, st);
+    const float2* C32 = nullptr;
+    if (P->Adf.p) {
+        // C = A X_prev with the double-float matrix; its head plane is C in FP32
+        P->Rdf.ensure(2 * (size_t)nm);
+        timed(P, 0, [&] { spmm_df(n, M->A.row_ptr.p, M->A.col.p, P->Adf.p, M->A.nnz, P->v32.p, P->Rdf.p, m, st); });
+        C32 = P->Rdf.p;
+    } else {
+        P->R.ensure(nm);
+        timed(P, 0, [&] { spmm<double2>(n, M->A.row_ptr.p, M->A.col.p, P->Aval.p, X, P->R.p, m, st); });
+        convert_c128_to_c64(nm, P->R.p, P->x32.p, st);
+        C32 = P->x32.p;
+    }
+    timed(P, 2, [&] {
+        P->rec_dropped = recycle_initial_guess(n, m, P->v32.p, C32, P->r32.p, P->x32.p, P->rc_scratch.p, st);
+    });
+    convert_c64_to_c128(nm, P->x32.p, X, st);
+}
 
 // True block FGMRES (one Krylov space for the m columns) with FP64 vectors;
 // the preconditioner M64 is the ORAS of the problem's precision
 void solve_block_krylov(mwi_problem* P, const OpFnT<double2>& A64, const OpFnT<double2>& M64, const double2* B,
-                        double2* X, int m, int restart, double t0, mwi_solve_info* info) {
+                        double2* X, int m, int restart, double t0, mwi_solve_info* info, bool x0) {
     const int64_t n = P->mesh->T.ndof;
     const int64_t nm = n * m;
     cudaStream_t st = P->st;
@@ -603,21 +642,29 @@ void solve_block_krylov(mwi_problem* P, const OpFnT<double2>& A64, const OpFnT<d
     std::vector<double> bn, rn, tol(m), est(m);
     col_norms(B, bn);
     for (int c = 0; c < m; ++c) tol[c] = o.rtol * bn[c];
-    MWI_CUDA(cudaMemsetAsync(X, 0, nm * sizeof(double2), st));
-    MWI_CUDA(cudaMemcpyAsync(P->R.p, B, nm * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     rn = bn;
+    auto converged = [&] {
+        A64(X, P->R.p);
+        residual_c128(nm, B, P->R.p, st);
+        col_norms(P->R.p, rn);
+        for (int c = 0; c < m; ++c)
+            if (bn[c] > 0 && rn[c] > o.rtol * bn[c]) return false;
+        return true;
+    };
+    bool done = false;
+    if (x0) {
+        done = converged();
+    } else {
+        MWI_CUDA(cudaMemsetAsync(X, 0, nm * sizeof(double2), st));
+        MWI_CUDA(cudaMemcpyAsync(P->R.p, B, nm * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    }
     int total = 0, deflated = 0;
-    while (true) {
+    while (!done) {
         int defl = 0;
         const int used = G.cycle(A64, M64, P->R.p, X, tol, std::min(restart, o.max_iter - total), st, est.data(), &defl);
         total += used;
         deflated += defl;
-        A64(X, P->R.p);
-        residual_c128(nm, B, P->R.p, st);
-        col_norms(P->R.p, rn);
-        bool done = true;
-        for (int c = 0; c < m; ++c)
-            if (bn[c] > 0 && rn[c] > o.rtol * bn[c]) done = false;
+        done = converged();
         if (done || total >= o.max_iter || used == 0) break;
     }
     int nconv = 0;
@@ -641,12 +688,17 @@ void solve_block_krylov(mwi_problem* P, const OpFnT<double2>& A64, const OpFnT<d
 }
 
 // solve A X = B for m columns in blocks of at most opts.max_block columns
-// (Krylov bases scale with the block width); X and B are [n][m]
-void solve_columns(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
+// (Krylov bases scale with the block width); X and B are [n][m].  recycled:
+// X holds the solution block of the previous, nearby system, whose span gives
+// the initial guess (only when the m columns form one block of at most 32)
+void solve_columns(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info,
+                   bool recycled = false) {
     // a shared block Krylov space costs m^2 per row in its Gram-Schmidt: at most 32 columns
     const int mb = P->opts.block_krylov ? std::min(P->opts.max_block, 32) : P->opts.max_block;
     if (m <= mb) {
-        solve_block(P, B, X, m, info);
+        const bool x0 = recycled && m <= 32;
+        if (x0) recycle_guess(P, B, X, m);
+        solve_block(P, B, X, m, info, x0);
         return;
     }
     const int64_t n = P->mesh->T.ndof;
@@ -681,7 +733,7 @@ void solve_columns(mwi_problem* P, const double2* B, double2* X, int m, mwi_solv
     if (notconv) throw Error(MWI_ENOTCONV, "FGMRES did not reach rtol on every column");
 }
 
-void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
+void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info, bool x0) {
     mwi_mesh* M = P->mesh;
     const int64_t n = M->T.ndof;
     const int64_t nm = n * m;
@@ -691,7 +743,7 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     const bool nested = o.precision == 2;
     const bool block = o.block_krylov != 0;
     if (mixed && !nested && !block) {
-        solve_block_df(P, B, X, m, info);
+        solve_block_df(P, B, X, m, info, x0);
         return;
     }
     DecompEntry& E = *P->dec;
@@ -762,30 +814,37 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     const double t0 = now_ms();
     P->inner_total = 0;
     if (block) {
-        solve_block_krylov(P, A64, M64, B, X, m, restart, t0, info);
+        solve_block_krylov(P, A64, M64, B, X, m, restart, t0, info, x0);
         return;
     }
     P->outer.column_norms2(B, b2, st);
     tolerances(m, b2, o.rtol, tol, bnorm, st);
     std::vector<double> bn(m), rn(m);
     MWI_CUDA(cudaMemcpyAsync(bn.data(), bnorm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MWI_CUDA(cudaMemsetAsync(X, 0, nm * sizeof(double2), st));
-    MWI_CUDA(cudaMemcpyAsync(P->R.p, B, nm * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    int total = 0;
-    bool done = false;
-    while (!done) {
-        int used = 0;
-        P->outer.cycle(A64, M64, P->R.p, X, tol, std::min(restart, o.max_iter - total), st, nullptr, &used);
-        total += used;
-        // true FP64 residual
+    // true FP64 residual; true when every column meets rtol
+    auto converged = [&] {
         A64(X, P->R.p);
         residual_c128(nm, B, P->R.p, st);
         P->outer.column_norms2(P->R.p, r2, st);
         MWI_CUDA(cudaMemcpyAsync(rn.data(), r2, m * sizeof(double), cudaMemcpyDeviceToHost, st));
         MWI_CUDA(cudaStreamSynchronize(st));
-        done = true;
         for (int c = 0; c < m; ++c)
-            if (bn[c] > 0 && std::sqrt(std::max(rn[c], 0.0)) > o.rtol * bn[c]) done = false;
+            if (bn[c] > 0 && std::sqrt(std::max(rn[c], 0.0)) > o.rtol * bn[c]) return false;
+        return true;
+    };
+    bool done = false;
+    if (x0) {
+        done = converged();
+    } else {
+        MWI_CUDA(cudaMemsetAsync(X, 0, nm * sizeof(double2), st));
+        MWI_CUDA(cudaMemcpyAsync(P->R.p, B, nm * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    }
+    int total = 0;
+    while (!done) {
+        int used = 0;
+        P->outer.cycle(A64, M64, P->R.p, X, tol, std::min(restart, o.max_iter - total), st, nullptr, &used);
+        total += used;
+        done = converged();
         if (total >= o.max_iter || used == 0) break;
     }
     int nconv = 0;
@@ -809,7 +868,7 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
 
 // MIXED: the complex FP32 ORAS preconditions an FGMRES whose basis, residual
 // and iterate are double-float planes (FP64-quality results on the FP32 pipes)
-void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info) {
+void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info, bool x0) {
     mwi_mesh* M = P->mesh;
     const int64_t n = M->T.ndof;
     const int64_t nm = n * m;
@@ -847,23 +906,32 @@ void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_sol
     tolerances(m, b2, o.rtol, tol, bnorm, st);
     std::vector<double> bn(m), rn(m);
     MWI_CUDA(cudaMemcpyAsync(bn.data(), bnorm, m * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MWI_CUDA(cudaMemsetAsync(P->Xdf.p, 0, 2 * nm * sizeof(float2), st));
-    MWI_CUDA(cudaMemcpyAsync(P->Rdf.p, P->Bdf.p, 2 * nm * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    int total = 0;
-    while (true) {
-        int used = 0;
-        G.cycle(Aop, Mop, P->Rdf.p, P->Xdf.p, tol, std::min(restart, o.max_iter - total), st, &used);
-        total += used;
-        // true residual in double-float
+    // true residual in double-float; true when every column meets rtol
+    auto converged = [&] {
         timed(P, 0, [&] {
             residual_df(n, M->A.row_ptr.p, M->A.col.p, P->Adf.p, nnz, P->Bdf.p, P->Xdf.p, P->Rdf.p, m, st);
         });
         G.norms2(P->Rdf.p, r2, st);
         MWI_CUDA(cudaMemcpyAsync(rn.data(), r2, m * sizeof(double), cudaMemcpyDeviceToHost, st));
         MWI_CUDA(cudaStreamSynchronize(st));
-        bool done = true;
         for (int c = 0; c < m; ++c)
-            if (bn[c] > 0 && std::sqrt(std::max(rn[c], 0.0)) > o.rtol * bn[c]) done = false;
+            if (bn[c] > 0 && std::sqrt(std::max(rn[c], 0.0)) > o.rtol * bn[c]) return false;
+        return true;
+    };
+    bool done = false;
+    if (x0) {
+        split_c128(nm, X, P->Xdf.p, st);
+        done = converged();
+    } else {
+        MWI_CUDA(cudaMemsetAsync(P->Xdf.p, 0, 2 * nm * sizeof(float2), st));
+        MWI_CUDA(cudaMemcpyAsync(P->Rdf.p, P->Bdf.p, 2 * nm * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    }
+    int total = 0;
+    while (!done) {
+        int used = 0;
+        G.cycle(Aop, Mop, P->Rdf.p, P->Xdf.p, tol, std::min(restart, o.max_iter - total), st, &used);
+        total += used;
+        done = converged();
         if (done || total >= o.max_iter || used == 0) break;
     }
     join_c128(nm, P->Xdf.p, X, st);
@@ -984,8 +1052,11 @@ mwi_status mwi_forward_solve(mwi_problem_t P, const mwi_antenna* tx, int32_t n_t
         launch_rhs(m, P->tx_dof_d.p, P->tx_sign_d.p, P->cur_d.p, 2.0 * kPi * P->freq * kMu0, P->Brhs.p, st);
         P->m_fwd = m;
         P->n_rx = n_rx;
+        const bool rec = P->opts.recycle && P->rec_m[0] == m;
+        P->rec_m[0] = 0;
         try {
-            solve_columns(P, P->Brhs.p, P->U.p, m, info);
+            solve_columns(P, P->Brhs.p, P->U.p, m, info, rec);
+            P->rec_m[0] = m;
         } catch (const Error& e) {
             if (e.status != MWI_ENOTCONV) throw;
             status = MWI_ENOTCONV;
@@ -1028,8 +1099,11 @@ static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const 
         MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));
         launch_adjoint_rhs(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->r_d.p, wd, P->Brhs.p, st);
         P->Lam.ensure(nm);
+        const bool rec = P->opts.recycle && P->rec_m[1] == m;
+        P->rec_m[1] = 0;
         try {
-            solve_columns(P, P->Brhs.p, P->Lam.p, m, info);
+            solve_columns(P, P->Brhs.p, P->Lam.p, m, info, rec);
+            P->rec_m[1] = m;
         } catch (const Error& e) {
             if (e.status != MWI_ENOTCONV) throw;
             status = MWI_ENOTCONV;
