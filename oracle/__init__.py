@@ -18,7 +18,8 @@ What it computes, in complex128, by the plain definitions:
 * the one-level ORAS preconditioner (Eq. ORAS) with the partition of unity of
   Section 3.2 (Eq. algebPartUnity, Eq. chi) and a right-preconditioned
   flexible GMRES, used where a direct solve is too large and to check the
-  preconditioner's pieces one by one (``dd``);
+  preconditioner's pieces one by one, and a two-level variant with a
+  geometric coarse space (Section 7) (``dd``);
 * the nodal (P1) permittivity parameter with the gradient penalty and the
   normalised misfit weights of Eq. defJ2 (``p1``);
 * block flexible GMRES, one Krylov space shared by the right-hand sides of a

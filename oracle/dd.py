@@ -19,12 +19,14 @@ Decomposition (Section 3):
   T_i^delta owning the face.
 
 ORAS (Eq. ORAS):  M^{-1} r = sum_i R_i^T D_i B_i^{-1} R_i r, each B_i^{-1} by
-sparse LU.  FGMRES: right-preconditioned flexible GMRES (restarted, x0 = 0,
+sparse LU.  Two-level variant (Section 7): a coarse Whitney space on a coarser
+mesh, Galerkin coarse operator, deflated combination with ORAS (CoarseSpace).  FGMRES: right-preconditioned flexible GMRES (restarted, x0 = 0,
 modified Gram-Schmidt Arnoldi, Givens rotations), stopped on the
 unpreconditioned relative residual (Section 6).
 """
 
 import numpy as np
+import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .assemble import _scatter_symmetric
@@ -213,3 +215,72 @@ def solve_oras(A, B, oras, rtol=1e-10, restart=50, maxiter=1000):
         U[:, j], it, _ = fgmres(A, B[:, j], oras.apply, rtol=rtol, restart=restart, maxiter=maxiter)
         its.append(it)
     return U, its
+
+
+class CoarseSpace:
+    """Two-level ORAS with a geometric coarse space (Section 7 names a
+    two-level preconditioner with a coarse space as what a one-level method
+    needs to scale to thousands of subdomains).
+
+    Coarse space: lowest-order Whitney elements on a coarser tetrahedral mesh
+    of the same domain.  The prolongation maps coarse DOFs to fine edge DOFs by
+    the fine edge's tangential integral of the coarse field, midpoint rule:
+      P[e, E] = N_E(m_e) . (x_hi(e) - x_lo(e)),
+    N_E evaluated in the coarse tet that contains the midpoint m_e (for a
+    midpoint outside the coarse mesh, the candidate tet with the largest
+    smallest barycentric coordinate, i.e. the affine extension of the nearest
+    tet's basis).  Coarse operator A_c = P^T A P (Galerkin; A is complex
+    symmetric, so P^T).  Deflated two-level preconditioner:
+      M_2 r = M_ORAS (r - A Q r) + Q r,   Q = P A_c^{-1} P^T.
+    """
+
+    def __init__(self, fine_xyz, fine_topo, coarse_xyz, coarse_topo, A, oras):
+        from scipy.spatial import cKDTree
+
+        from .fem import bary_gradients
+        from .topology import LOCAL_EDGES
+
+        ctv = coarse_topo.tv
+        P4 = coarse_xyz[ctv]
+        G, _ = bary_gradients(P4)
+        cen = P4.mean(axis=1)
+        e = fine_topo.edges
+        fdof = np.full(e.shape[0], -1, dtype=np.int64)
+        fdof[fine_topo.tet_edges.ravel()] = fine_topo.tet_dofs[:, :6].ravel()
+        live = np.nonzero(fdof >= 0)[0]
+        mid = 0.5 * (fine_xyz[e[live, 0]] + fine_xyz[e[live, 1]])
+        tang = fine_xyz[e[live, 1]] - fine_xyz[e[live, 0]]
+        k = min(12, ctv.shape[0])
+        _, cand = cKDTree(cen).query(mid, k=k)
+        cand = cand.reshape(live.size, k)
+        # barycentric coordinates of every midpoint in every candidate: lambda_a is
+        # affine with gradient G_a and equals 1/4 at the centroid
+        lam = np.einsum("nkad,nkd->nka", G[cand], mid[:, None, :] - cen[cand]) + 0.25
+        mins = lam.min(axis=2)
+        inside = mins >= -1e-12
+        pick = np.where(inside.any(axis=1), inside.argmax(axis=1), mins.argmax(axis=1))
+        t = cand[np.arange(live.size), pick]
+        L = lam[np.arange(live.size), pick]
+        rows, cols, vals = [], [], []
+        for j, (a, b) in enumerate(LOCAL_EDGES):
+            N = L[:, a, None] * G[t, b] - L[:, b, None] * G[t, a]
+            cd = coarse_topo.tet_dofs[t, j]
+            ok = cd >= 0
+            rows.append(fdof[live][ok])
+            cols.append(cd[ok])
+            vals.append(np.einsum("nd,nd->n", N[ok], tang[ok]))
+        self.P = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                               shape=(fine_topo.ndof, coarse_topo.ndof)).tocsr()
+        self.A = A
+        self.oras = oras
+        self.Ac = (self.P.T @ A @ self.P).tocsc()
+        self.lu = spla.splu(self.Ac, permc_spec="MMD_AT_PLUS_A")
+
+    def coarse_correction(self, r):
+        """Q r = P A_c^{-1} P^T r."""
+        return self.P @ self.lu.solve(np.asarray(self.P.T @ r, dtype=np.complex128))
+
+    def apply(self, r):
+        """Deflated two-level preconditioner M_ORAS (r - A Q r) + Q r."""
+        q = self.coarse_correction(r)
+        return self.oras.apply(r - self.A @ q) + q
