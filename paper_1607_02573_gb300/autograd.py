@@ -43,7 +43,9 @@ def lbfgs_invert(problem, eps0, tx, rx, S_meas, w=None, iters=10, lr=1.0, histor
     """Minimise J over eps with torch.optim.LBFGS (strong-Wolfe line search).
 
     Returns the reconstructed eps (complex128 numpy) and the list of J values
-    of every function evaluation.
+    of every function evaluation.  A problem created with recycle=1 starts every
+    evaluation's forward and adjoint solves from the span of the previous
+    evaluation's solutions (fewer iterations, same tolerance).
     """
     x = torch.from_numpy(np.stack([np.real(eps0), np.imag(eps0)]).astype(np.float64)).requires_grad_(True)
     opt = torch.optim.LBFGS([x], lr=lr, max_iter=iters, history_size=history, line_search_fn="strong_wolfe",

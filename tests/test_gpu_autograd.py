@@ -68,15 +68,23 @@ def test_directional_derivative_matches_finite_difference(lib):
 
 
 def test_lbfgs_reduces_misfit(lib):
+    """Four L-BFGS iterations, with and without recycling of the previous
+    evaluation's solutions: both reduce the misfit, and since every solve runs
+    to rtol 1e-10 the two take the same path (same J values to 1e-6)."""
     mwi, ag = lib
     from synthetic import chamber_target_eps
     mesh, eps, tx, rx = chamber_case(12, 11, n_ant=8)
     target = chamber_target_eps(mesh.xyz, mesh.tet)
     M = mwi.Mesh(mesh.xyz, mesh.tet, mesh.bface_tag)
-    P = mwi.Problem(M, target, FREQ, n_sub=4, rtol=1e-10, precision=1)
-    S_meas = P.forward_solve(tx, rx)
-    eps0 = np.full(mesh.nt, 44 - 20j)
-    rec, values = ag.lbfgs_invert(P, eps0, tx, rx, S_meas, iters=4)
-    assert values[-1] < 0.5 * values[0]
-    assert np.all(np.isfinite(rec))
-    P.close()
+    runs = {}
+    for recycle in (0, 1):
+        P = mwi.Problem(M, target, FREQ, n_sub=4, rtol=1e-10, precision=1, recycle=recycle)
+        S_meas = P.forward_solve(tx, rx)
+        eps0 = np.full(mesh.nt, 44 - 20j)
+        rec, values = ag.lbfgs_invert(P, eps0, tx, rx, S_meas, iters=4)
+        assert values[-1] < 0.5 * values[0]
+        assert np.all(np.isfinite(rec))
+        runs[recycle] = values
+        P.close()
+    assert len(runs[0]) == len(runs[1])
+    assert np.allclose(runs[0], runs[1], rtol=1e-6, atol=0)
