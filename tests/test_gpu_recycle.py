@@ -103,3 +103,27 @@ def test_same_system_again_starts_from_its_solution(lib, chamber):
     assert P.info.iters_max <= 1 < first
     assert col_rel_err(P.fields_host(0), ref2["U"][perm]).max() <= 1e-5
     P.close()
+
+
+def test_recycling_edge_cases(lib, chamber):
+    """A changed transmitter count does not recycle (different block shape) and
+    still solves; recycling composes with the true block solver; one column."""
+    mesh, eps, eps2, tx, rx, M, topo, perm, ref2 = chamber
+    P = lib.Problem(M, eps, FREQ, n_sub=6, precision=0, recycle=1, block_krylov=1, rtol=1e-12, max_iter=300)
+    P.forward_solve(tx[:3], rx)
+    P.update_eps(eps2)
+    S = P.forward_solve(tx, rx)  # 6 columns after 3: starts from zero
+    assert P.info.n_converged == tx.shape[0] and P.info.iters_max > 0
+    assert col_rel_err(P.fields_host(0), ref2["U"][perm]).max() <= 1e-8
+    assert rel_err(S, ref2["S"]) <= 1e-8
+    first = P.info.iters_max
+    S = P.forward_solve(tx, rx)  # same 6 columns again: recycled into the block solver
+    assert P.info.iters_max < first
+    assert col_rel_err(P.fields_host(0), ref2["U"][perm]).max() <= 1e-8
+    P.close()
+    P = lib.Problem(M, eps2, FREQ, n_sub=6, precision=1, recycle=1, block_krylov=1, rtol=1e-9, max_iter=300)
+    for _ in range(2):
+        S = P.forward_solve(tx[2:3], rx)
+        assert P.info.n_converged == 1
+        assert col_rel_err(P.fields_host(0), ref2["U"][perm][:, 2:3]).max() <= 1e-6
+    P.close()
