@@ -322,6 +322,24 @@ def cpu_baseline(args, steps=1):
                       f"({mesh.nt} tets, {topo.ndof} DOF), 32+32 columns; {dt:.1f} s per step"}
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """The largest value over all ranks (a job's time is its slowest rank's);
+    every rank gets it.  The process group must be initialised when world > 1."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, n_cols, steps, ms):
+    """RHS-solves per second of the whole job: every replica solves n_cols
+    columns per step, and the job takes ms for its steps."""
+    return world * n_cols * steps / (ms / 1e3)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -352,12 +370,8 @@ def main():
         dist.init_process_group("nccl", rank=rank, world_size=world)
     mesh, M, R = run_mine(args, rank, world)
     mx = R["mixed"]
-    ms = mx["ms"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * mx["n_cols"] * mx["steps"] / (ms / 1e3)
+    ms = max_over_ranks(mx["ms"], world, "cuda")
+    value = whole_job_value(world, mx["n_cols"], mx["steps"], ms)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
