@@ -24,6 +24,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -51,6 +52,7 @@ def parse():
     ap.add_argument("--n-ant", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nd-leaf", type=int, default=64)
+    ap.add_argument("--clocks-csv", default=None, help="directory for the nvidia-smi clock samples (CSV)")
     ap.add_argument("--recycle-steps", type=int, default=3,
                     help="timed gradient steps with Krylov recycling across steps (0: skip)")
     ap.add_argument("--block-steps", type=int, default=1,
@@ -68,10 +70,13 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 
 
 class ClockSampler:
+    # samples go to a CSV beside the run (--clocks-csv DIR) or to the temp directory
+    out_dir = None
+
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(ClockSampler.out_dir or tempfile.gettempdir(), f"mwi_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -342,6 +347,7 @@ def whole_job_value(world, n_cols, steps, ms):
 
 def main():
     args = parse()
+    ClockSampler.out_dir = args.clocks_csv
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
