@@ -430,9 +430,10 @@ def main():
                           "kernel_ms_per_step": {k: round(v / R["recycle"]["steps"], 3) for k, v in
                                                  zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"],
                                                      R["recycle"]["kernel_ms"])},
-                          "what": "the main line's gradient steps with recycle = 1: each forward (adjoint) "
-                                  "solve starts from the least-residual element of the previous step's "
-                                  "forward (adjoint) solution span"} if R.get("recycle") else None},
+                          "what": "the main line's gradient steps with recycle = 1: each forward solve starts "
+                                  "from the least-residual element of the span of the previous step's forward "
+                                  "solutions, each adjoint solve from that of the current forward and the "
+                                  "previous adjoint solutions"} if R.get("recycle") else None},
     }
     if R["fp64"]:
         f = R["fp64"]

@@ -107,13 +107,16 @@ typedef struct {
                              deflated); the preconditioner is the ORAS of `precision`.
                              iters_max then counts block steps.  Other values: MWI_EINVAL */
     int32_t recycle;      /* 1 = Krylov recycling across a sequence of nearby systems (the
-                             recycling of Section 7): a forward (adjoint) solve whose
-                             transmitter count m <= 32 equals the previous converged forward
-                             (adjoint) solve's starts every column from the least-residual
-                             element of the span of the previous solution block (FP32
-                             projection, x0 = X_prev Y, Y = argmin ||B - A X_prev Y||); the
-                             solve then runs to rtol as usual, and iters_max is 0 when the
-                             guess already meets it.  Its SpMM counts in the SpMM timer and
+                             recycling of Section 7): a forward solve whose transmitter count
+                             m <= 32 equals the previous converged forward solve's starts every
+                             column from the least-residual element of the span of the previous
+                             forward solutions (FP32 projection, x0 = X Y,
+                             Y = argmin ||B - A X Y||); an adjoint solve uses the span of the
+                             current forward solutions and, when the previous adjoint solve had
+                             the same m, of the previous adjoint solutions (when the receivers
+                             are among the transmitters the adjoint solution lies in the first
+                             span).  The solve then runs to rtol as usual, and iters_max is 0
+                             when the guess already meets it.  Its SpMM counts in the SpMM timer and
                              its projection in the orthogonalisation timer.  0 = off [0];
                              other values: MWI_EINVAL */
 } mwi_solver_opts;

@@ -126,7 +126,7 @@ struct mwi_problem {
     // as the recycled space of the next solve (0 = none)
     int rec_m[2] = {0, 0};
     int rec_dropped = 0;
-    DevBuf<double2> rc_scratch;
+    DevBuf<double2> rc_scratch, rc_block;
     DevBuf<float2> Adf, Bdf, Xdf, Rdf;   // double-float planes
     DevBuf<double2> U, Lam, Brhs, R, Bc, Xc;
     DevBuf<float2> v32, x32, r32;
@@ -587,34 +587,48 @@ void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<in
 void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info, bool x0 = false);
 void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info, bool x0);
 
-// On entry X holds the previous system's solution block (m <= 32 columns); on
-// exit the least-residual element of its span for every column of B (the
-// recycled initial guess, in FP32 arithmetic)
-void recycle_guess(mwi_problem* P, const double2* B, double2* X, int m) {
+// The recycled space is the me columns of extra (when not null: the current
+// forward solutions, for an adjoint solve) followed by the m columns X holds on
+// entry (when prev: the previous system's solution block); on exit X holds,
+// for every column of B, the least-residual element of that span (the
+// recycled initial guess, in FP32 arithmetic).  m <= 32, m + me <= 64.  The
+// projection keeps columns greedily in this order, so the current system's
+// solutions come first.
+void recycle_guess(mwi_problem* P, const double2* B, double2* X, int m, bool prev, const double2* extra,
+                   int me) {
     mwi_mesh* M = P->mesh;
     const int64_t n = M->T.ndof;
     const int64_t nm = n * m;
+    const int k = (prev ? m : 0) + (extra ? me : 0);
+    const int64_t nk = n * k;
     cudaStream_t st = P->st;
-    P->v32.ensure(nm);
-    P->x32.ensure(nm);
+    // the recycled block [X | extra] as one [n][k] FP64 array, then in FP32
+    P->rc_block.ensure(nk);
+    if (extra) copy_columns(n, me, 0, me, extra, k, 0, P->rc_block.p, st);
+    if (prev) copy_columns(n, m, 0, m, X, k, extra ? me : 0, P->rc_block.p, st);
+    P->v32.ensure(nk);
+    P->x32.ensure(std::max(nk, nm));
     P->r32.ensure(nm);
-    P->rc_scratch.ensure(recycle_scratch_entries(m));
-    convert_c128_to_c64(nm, X, P->v32.p, st);
+    P->rc_scratch.ensure(recycle_scratch_entries(k, m));
+    convert_c128_to_c64(nk, P->rc_block.p, P->v32.p, st);
     convert_c128_to_c64(nm, B, P->r32.p, st);
     const float2* C32 = nullptr;
     if (P->Adf.p) {
-        // C = A X_prev with the double-float matrix; its head plane is C in FP32
-        P->Rdf.ensure(2 * (size_t)nm);
-        timed(P, 0, [&] { spmm_df(n, M->A.row_ptr.p, M->A.col.p, P->Adf.p, M->A.nnz, P->v32.p, P->Rdf.p, m, st); });
+        // C = A X_rec with the double-float matrix; its head plane is C in FP32
+        P->Rdf.ensure(2 * (size_t)nk);
+        timed(P, 0, [&] { spmm_df(n, M->A.row_ptr.p, M->A.col.p, P->Adf.p, M->A.nnz, P->v32.p, P->Rdf.p, k, st); });
         C32 = P->Rdf.p;
     } else {
-        P->R.ensure(nm);
-        timed(P, 0, [&] { spmm<double2>(n, M->A.row_ptr.p, M->A.col.p, P->Aval.p, X, P->R.p, m, st); });
-        convert_c128_to_c64(nm, P->R.p, P->x32.p, st);
+        P->R.ensure(nk);
+        timed(P, 0, [&] {
+            spmm<double2>(n, M->A.row_ptr.p, M->A.col.p, P->Aval.p, P->rc_block.p, P->R.p, k, st);
+        });
+        convert_c128_to_c64(nk, P->R.p, P->x32.p, st);
         C32 = P->x32.p;
     }
+    // x0 is written to x32 after the projection has consumed C (which x32 holds in the FP64-matrix case)
     timed(P, 2, [&] {
-        P->rec_dropped = recycle_initial_guess(n, m, P->v32.p, C32, P->r32.p, P->x32.p, P->rc_scratch.p, st);
+        P->rec_dropped = recycle_initial_guess(n, k, m, P->v32.p, C32, P->r32.p, P->x32.p, P->rc_scratch.p, st);
     });
     convert_c64_to_c128(nm, P->x32.p, X, st);
 }
@@ -692,12 +706,12 @@ void solve_block_krylov(mwi_problem* P, const OpFnT<double2>& A64, const OpFnT<d
 // X holds the solution block of the previous, nearby system, whose span gives
 // the initial guess (only when the m columns form one block of at most 32)
 void solve_columns(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info,
-                   bool recycled = false) {
+                   bool recycled = false, const double2* extra = nullptr) {
     // a shared block Krylov space costs m^2 per row in its Gram-Schmidt: at most 32 columns
     const int mb = P->opts.block_krylov ? std::min(P->opts.max_block, 32) : P->opts.max_block;
     if (m <= mb) {
-        const bool x0 = recycled && m <= 32;
-        if (x0) recycle_guess(P, B, X, m);
+        const bool x0 = (recycled || extra) && m <= 32;
+        if (x0) recycle_guess(P, B, X, m, recycled, extra, m);
         solve_block(P, B, X, m, info, x0);
         return;
     }
@@ -1099,10 +1113,14 @@ static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const 
         MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));
         launch_adjoint_rhs(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->r_d.p, wd, P->Brhs.p, st);
         P->Lam.ensure(nm);
+        // recycled space of the adjoint solve: the previous adjoint solutions and
+        // the current forward solutions (whose span holds the adjoint solution
+        // exactly when the receivers are among the transmitters)
         const bool rec = P->opts.recycle && P->rec_m[1] == m;
+        const double2* fwd = P->opts.recycle && P->rec_m[0] == m ? P->U.p : nullptr;
         P->rec_m[1] = 0;
         try {
-            solve_columns(P, P->Brhs.p, P->Lam.p, m, info, rec);
+            solve_columns(P, P->Brhs.p, P->Lam.p, m, info, rec, fwd);
             P->rec_m[1] = m;
         } catch (const Error& e) {
             if (e.status != MWI_ENOTCONV) throw;

@@ -163,14 +163,14 @@ template <typename C>
 void spmm(int64_t n, const int32_t* row_ptr, const int32_t* col, const C* val, const C* x, C* y, int m,
           cudaStream_t st);
 
-// Initial guess from a recycled subspace: x0 = X_prev Y with
-// Y = argmin ||B - C Y|| (C = A X_prev), FP32 products, FP64 chunk sums, the
-// m x m normal equations by Cholesky on the host (m <= 32).  scratch holds
-// recycle_scratch_entries(m) entries.  Returns the number of recycled columns
-// left out as numerically dependent.
+// Initial guess from a recycled subspace: x0 = X_rec Y with
+// Y = argmin ||B - C Y|| (C = A X_rec; X_rec, C [n][k], k <= 64; B, x0 [n][m],
+// m <= 32), FP32 products, FP64 chunk sums, the k x k normal equations by
+// Cholesky on the host.  scratch holds recycle_scratch_entries(k, m) entries.
+// Returns the number of recycled columns left out as numerically dependent.
 constexpr int kRecycleChunks = 1216;
-size_t recycle_scratch_entries(int m);
-int recycle_initial_guess(int64_t n, int m, const float2* X32, const float2* C32, const float2* B32, float2* x0,
-                          double2* scratch, cudaStream_t st);
+size_t recycle_scratch_entries(int k, int m);
+int recycle_initial_guess(int64_t n, int k, int m, const float2* X32, const float2* C32, const float2* B32,
+                          float2* x0, double2* scratch, cudaStream_t st);
 
 }  // namespace mwi

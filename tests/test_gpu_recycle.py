@@ -127,3 +127,27 @@ def test_recycling_edge_cases(lib, chamber):
         assert P.info.n_converged == 1
         assert col_rel_err(P.fields_host(0), ref2["U"][perm][:, 2:3]).max() <= 1e-6
     P.close()
+
+
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6)])
+def test_adjoint_recycles_forward_solutions(lib, chamber, precision, rtol, tol):
+    """Receivers = transmitters: the adjoint right-hand sides lie in the span of
+    the forward ones, so the adjoint solutions lie in the span of the forward
+    solutions, and the first adjoint solve (no previous adjoint) starts next to
+    them (to the accuracy of the FP32 projection)."""
+    mesh, eps, eps2, tx, rx, M, topo, perm, ref2 = chamber
+    rng = np.random.default_rng(23)
+    S_meas = ref2["S"] * (1 + 0.1 * rng.standard_normal(ref2["S"].shape))
+    J_o, grad_o, extra = O.misfit_and_gradient(mesh.xyz, topo, eps2, FREQ, tx, rx, S_meas, fwd=ref2)
+    its = {}
+    for rec in (0, 1):
+        P = lib.Problem(M, eps2, FREQ, n_sub=6, precision=precision, recycle=rec, rtol=rtol, max_iter=300)
+        P.forward_solve(tx, rx)
+        J, grad = P.misfit_and_gradient(S_meas)
+        its[rec] = P.info.iters_max
+        assert abs(J - J_o) <= tol * abs(J_o)
+        assert rel_err(grad, grad_o) <= tol
+        assert col_rel_err(P.fields_host(1), extra["Lam"][perm]).max() <= tol
+        P.close()
+    # the FP32 projection leaves ~1e-7 of the residual: a few steps remain at these tolerances
+    assert its[1] <= its[0] // 2, its
