@@ -147,9 +147,10 @@ def run_mine(args, rank, world):
     eps_d = torch.from_numpy(eps).to(dev)
     results = {}
 
-    def one_arm(precision, steps, warmup, e2e_steps, recycle=0):
+    def one_arm(precision, steps, warmup, e2e_steps, recycle=0, factor_reuse=0):
         P = mwi.Problem(M, eps_d, FREQ, stream=stream, n_sub=64, precision=precision, rtol=RTOL,
-                        verbose=2, max_iter=500, nd_leaf=args.nd_leaf, sweep_engine=args.engine, recycle=recycle)
+                        verbose=2, max_iter=500, nd_leaf=args.nd_leaf, sweep_engine=args.engine, recycle=recycle,
+                        factor_reuse=factor_reuse)
         fs = P.factor_stats()
         fs["oras_bytes_per_call"] = P.oras_traffic(min(32, args.n_ant))
         # synthetic measurements: S of the two-inclusion target map plus 1 % noise
@@ -232,6 +233,9 @@ def run_mine(args, rank, world):
     # Krylov recycling: the same step sequence (eps_r alternating between two maps 1 % apart, as
     # consecutive L-BFGS steps), every solve starting from the previous step's solution span
     results["recycle"] = one_arm(1, args.recycle_steps, args.warmup, 0, recycle=1) if args.recycle_steps > 0 else None
+    # and keeping the subdomain factors for two of every three steps (factor_reuse = 2)
+    results["reuse"] = (one_arm(1, args.recycle_steps, args.warmup, 0, recycle=1, factor_reuse=2)
+                        if args.recycle_steps > 0 else None)
     # true block FGMRES (one Krylov space for the 32 columns) against the
     # pseudo-block FGMRES on the same forward solve of the 32 transmitters
     if args.block_steps > 0:
@@ -433,7 +437,20 @@ def main():
                           "what": "the main line's gradient steps with recycle = 1: each forward solve starts "
                                   "from the least-residual element of the span of the previous step's forward "
                                   "solutions, each adjoint solve from that of the current forward and the "
-                                  "previous adjoint solutions"} if R.get("recycle") else None},
+                                  "previous adjoint solutions"} if R.get("recycle") else None,
+                      "recycling_with_factor_reuse": {
+                          "value": round(R["reuse"]["value"], 3), "unit": UNIT,
+                          "ms_per_step": round(R["reuse"]["ms_per_step"], 2), "steps": R["reuse"]["steps"],
+                          "fwd_iterations": R["reuse"]["fwd_info"]["iters_max"],
+                          "adj_iterations": R["reuse"]["adj_info"]["iters_max"],
+                          "converged_columns": R["reuse"]["converged"],
+                          "expected_columns": R["reuse"]["expected"],
+                          "kernel_ms_per_step": {k: round(v / R["reuse"]["steps"], 3) for k, v in
+                                                 zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"],
+                                                     R["reuse"]["kernel_ms"])},
+                          "what": "as krylov_recycling, with factor_reuse = 2: two of every three eps_r updates "
+                                  "keep the previous subdomain factors as the preconditioner"}
+                      if R.get("reuse") else None},
     }
     if R["fp64"]:
         f = R["fp64"]

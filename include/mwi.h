@@ -119,6 +119,12 @@ typedef struct {
                              when the guess already meets it.  Its SpMM counts in the SpMM timer and
                              its projection in the orthogonalisation timer.  0 = off [0];
                              other values: MWI_EINVAL */
+    int32_t factor_reuse; /* mwi_update_eps[_device]: up to this many consecutive updates
+                             reassemble A for the new eps_r but keep the previous subdomain
+                             factors as the ORAS preconditioner (a preconditioner for a
+                             nearby operator: more iterations, same rtol on the new system);
+                             the next update refactors.  0 = refactor on every update [0];
+                             < 0: MWI_EINVAL */
 } mwi_solver_opts;
 
 typedef struct {

@@ -127,6 +127,7 @@ struct mwi_problem {
     int rec_m[2] = {0, 0};
     int rec_dropped = 0;
     DevBuf<double2> rc_scratch, rc_block;
+    int reuse_count = 0;  // eps_r updates since the factors were computed
     DevBuf<float2> Adf, Bdf, Xdf, Rdf;   // double-float planes
     DevBuf<double2> U, Lam, Brhs, R, Bc, Xc;
     DevBuf<float2> v32, x32, r32;
@@ -199,6 +200,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     if (d.sweep_engine <= 0) d.sweep_engine = 2;
     if (d.block_krylov < 0 || d.block_krylov > 1) throw Error(MWI_EINVAL, "block_krylov must be 0 or 1");
     if (d.recycle < 0 || d.recycle > 1) throw Error(MWI_EINVAL, "recycle must be 0 or 1");
+    if (d.factor_reuse < 0) throw Error(MWI_EINVAL, "factor_reuse must be >= 0");
     return d;
 }
 
@@ -453,7 +455,10 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
 }
 
 // assemble A and B_i values for the current eps, then factorise
-void numeric_setup(mwi_problem* P) {
+// assemble A for the current eps_r; with refactor, also the subdomain
+// matrices B_i and their factors (otherwise the previous factors stay as the
+// ORAS preconditioner)
+void numeric_setup(mwi_problem* P, bool refactor = true) {
     mwi_mesh* M = P->mesh;
     const Topology& T = M->T;
     cudaStream_t st = P->st;
@@ -471,6 +476,11 @@ void numeric_setup(mwi_problem* P) {
         split_c128(M->A.nnz, P->Aval.p, P->Adf.p, st);
     }
     DecompEntry& E = *P->dec;
+    if (!refactor) {
+        MWI_CUDA(cudaStreamSynchronize(st));
+        P->setup_ms = now_ms() - t0;
+        return;
+    }
     P->B_coef.ensure(std::max<size_t>(1, E.D.B_faces.face.size()));
     launch_face_coef(E.fu_tet.p, (int64_t)E.D.B_faces.face.size(), P->eps.p, P->k0, P->B_coef.p, st);
     P->Bval.ensure(E.B.nnz);
@@ -1029,7 +1039,10 @@ static void update_eps(mwi_problem_t P, const double* eps, bool dev) {
             MWI_REQUIRE(std::isfinite(eps[2 * t]) && std::isfinite(eps[2 * t + 1]), MWI_EINVAL, "eps_r not finite");
     MWI_CUDA(cudaMemcpyAsync(P->eps.p, eps, nt * sizeof(double2),
                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, P->st));
-    numeric_setup(P);
+    // factor reuse: up to factor_reuse consecutive updates keep the factors
+    const bool refactor = P->opts.factor_reuse <= 0 || P->reuse_count >= P->opts.factor_reuse;
+    numeric_setup(P, refactor);
+    P->reuse_count = refactor ? 0 : P->reuse_count + 1;
     P->have_fwd = false;
     P->have_adj = false;
 }

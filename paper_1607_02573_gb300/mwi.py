@@ -38,7 +38,7 @@ class mwi_solver_opts(C.Structure):
                 ("overlap", C.c_int32), ("precision", C.c_int32), ("inner_iters", C.c_int32),
                 ("inner_rtol", C.c_double), ("nd_leaf", C.c_int32), ("verbose", C.c_int32),
                 ("part", C.POINTER(C.c_int32)), ("max_block", C.c_int32), ("sweep_engine", C.c_int32),
-                ("block_krylov", C.c_int32), ("recycle", C.c_int32)]
+                ("block_krylov", C.c_int32), ("recycle", C.c_int32), ("factor_reuse", C.c_int32)]
 
 
 class mwi_solve_info(C.Structure):

@@ -151,3 +151,26 @@ def test_adjoint_recycles_forward_solutions(lib, chamber, precision, rtol, tol):
         P.close()
     # the FP32 projection leaves ~1e-7 of the residual: a few steps remain at these tolerances
     assert its[1] <= its[0] // 2, its
+
+
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6)])
+def test_factor_reuse_solves_the_new_system(lib, chamber, precision, rtol, tol):
+    """factor_reuse = 1: the first eps_r update keeps the previous factors as
+    the preconditioner of the new operator, the second refactors; both solves
+    match the direct oracle solution of the new system."""
+    mesh, eps, eps2, tx, rx, M, topo, perm, ref2 = chamber
+    P = lib.Problem(M, eps, FREQ, n_sub=6, precision=precision, factor_reuse=1, rtol=rtol, max_iter=300)
+    P.forward_solve(tx, rx)
+    its = []
+    for _ in range(2):
+        P.update_eps(eps2)
+        S = P.forward_solve(tx, rx)
+        assert P.info.n_converged == tx.shape[0]
+        its.append(P.info.iters_max)
+        assert col_rel_err(P.fields_host(0), ref2["U"][perm]).max() <= tol
+        assert rel_err(S, ref2["S"]) <= tol
+    assert its[1] <= its[0], its  # the refactored preconditioner is the exact one
+    P.close()
+    with pytest.raises(lib.MwiError) as e:
+        lib.Problem(M, eps, FREQ, n_sub=6, factor_reuse=-1)
+    assert e.value.status == lib.MWI_EINVAL
