@@ -34,3 +34,35 @@ def test_library_exports_every_declared_symbol():
 def test_last_error_is_callable_without_gpu():
     from paper_1607_02573_gb300 import mwi
     assert isinstance(mwi.mwi_last_error(), bytes)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the C header's sizes and field
+    offsets (a field added on one side only would pass garbage across the ABI)."""
+    import shutil
+    import subprocess
+
+    import pytest
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1607_02573_gb300 import mwi
+    structs = {"mwi_solver_opts": mwi.mwi_solver_opts, "mwi_solve_info": mwi.mwi_solve_info,
+               "mwi_antenna": mwi.mwi_antenna}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mwi.h"', "int main(void) {"]
+    for name, st in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        name, what, val = line.split()
+        st = structs[name]
+        want = ctypes.sizeof(st) if what == "size" else getattr(st, what).offset
+        assert int(val) == want, (name, what, int(val), want)
