@@ -194,7 +194,12 @@ class Mesh:
 
 
 class Problem:
-    """Owns an mwi_problem_t (assembled operator, ORAS factors, resident fields)."""
+    """Owns an mwi_problem_t (assembled operator, ORAS factors, resident fields).
+
+    Keyword options are the fields of mwi_solver_opts (include/mwi.h): rtol,
+    max_iter, restart, n_sub, overlap, precision (0 FP64, 1 mixed, 2 nested),
+    inner_iters, inner_rtol, nd_leaf, verbose, part, max_block, sweep_engine,
+    block_krylov, recycle, factor_reuse; an unknown name raises TypeError."""
 
     def __init__(self, mesh, eps, freq, stream=None, **opts):
         import torch
