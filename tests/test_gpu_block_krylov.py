@@ -100,3 +100,17 @@ def test_repeated_transmitter_is_deflated(lib, chamber):
     assert col_rel_err(U, Uo).max() <= 1e-7
     assert rel_err(S, ref["S"][:, [0, 1, 2, 1]]) <= 1e-7  # [receiver, transmitter]
     P.close()
+
+
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-11, 1e-8), (1, 1e-9, 1e-6)])
+def test_restarted_block_solver(lib, chamber, precision, rtol, tol):
+    """Restart length 2: many block cycles, each from the true residual with a
+    fresh block basis; the result still matches the direct oracle."""
+    mesh, eps, tx, rx, M, topo, perm, ref = chamber
+    P = lib.Problem(M, eps, FREQ, n_sub=6, precision=precision, block_krylov=1, restart=2, rtol=rtol, max_iter=400)
+    S = P.forward_solve(tx, rx)
+    assert P.info.n_converged == tx.shape[0]
+    assert P.info.iters_max > 2
+    assert col_rel_err(P.fields_host(0), ref["U"][perm]).max() <= tol
+    assert rel_err(S, ref["S"]) <= tol
+    P.close()
