@@ -68,7 +68,7 @@ def test_recycled_guess_matches_oracle(lib, chamber):
     P.close()
 
 
-@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6)])
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6), (2, 1e-9, 1e-6)])
 def test_recycled_solve_matches_direct_oracle(lib, chamber, precision, rtol, tol):
     mesh, eps, eps2, tx, rx, M, topo, perm, ref2 = chamber
     rng = np.random.default_rng(22)
@@ -174,3 +174,25 @@ def test_factor_reuse_solves_the_new_system(lib, chamber, precision, rtol, tol):
     with pytest.raises(lib.MwiError) as e:
         lib.Problem(M, eps, FREQ, n_sub=6, factor_reuse=-1)
     assert e.value.status == lib.MWI_EINVAL
+
+
+def test_recycling_order2(lib):
+    """Second-order elements: recycled solves of a perturbed system against the
+    direct oracle (mixed path, rtol 1e-9 -> <= 1e-6)."""
+    from tests._helpers import cube_case
+    mesh, eps, tx, rx = cube_case(4)
+    M = lib.Mesh(mesh.xyz, mesh.tet, mesh.bface_tag, order=2)
+    topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, 2)
+    kind, verts = M.dof_keys()
+    perm = key_perm(kind, verts, topo)
+    eps2 = eps * (1 + 0.03 * np.random.default_rng(24).uniform(-1, 1, mesh.nt))
+    ref2 = O.forward(mesh.xyz, topo, eps2, FREQ, tx, rx)
+    P = lib.Problem(M, eps, FREQ, n_sub=3, precision=1, recycle=1, rtol=1e-9, max_iter=300)
+    P.forward_solve(tx, rx)
+    P.update_eps(eps2)
+    S = P.forward_solve(tx, rx)
+    assert P.info.n_converged == tx.shape[0]
+    assert col_rel_err(P.fields_host(0), ref2["U"][perm]).max() <= 1e-6
+    assert rel_err(S, ref2["S"]) <= 1e-6
+    P.close()
+    M.close()
