@@ -304,6 +304,12 @@ mwi_status mwi_p1_gradient(mwi_mesh_t mesh, const double* grad_tet_dev, const do
  * complex FP32 modes and 16 in FP64. */
 mwi_status mwi_oras_traffic(mwi_problem_t prob, int32_t m, double* bytes);
 
+/* Device memory held by a problem: its operator, subdomain factors, field
+ * blocks and solver workspaces (buffers grow with the widest solve so far);
+ * the mesh and its decomposition, shared by the problems on that mesh, are not
+ * counted.  For admission against a memory budget (a serving cache). */
+mwi_status mwi_problem_device_bytes(mwi_problem_t prob, int64_t* bytes);
+
 /* Per-kernel timing since the last reset, from CUDA events recorded on the
  * problem's stream around every call (no synchronisation in between):
  * ms[0] SpMM, ms[1] ORAS apply, ms[2] orthogonalisation (CGS2 + norms),

@@ -154,6 +154,19 @@ struct mwi_problem {
         for (auto& e : ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
         for (auto e : ev_free) cudaEventDestroy(e);
     }
+    // device bytes held by this problem (the mesh and its decomposition are shared)
+    size_t device_bytes() const {
+        size_t b = eps.bytes() + A_coef.bytes() + B_coef.bytes() + Aval.bytes() + Bval.bytes() + Aval32.bytes() +
+                   ws64.bytes() + inv64.bytes() + ws32.bytes() + inv32.bytes() + perturbed.bytes() + Y64.bytes() +
+                   Z64.bytes() + upd64.bytes() + Y32.bytes() + Z32.bytes() + upd32.bytes() + outer.bytes() +
+                   inner.bytes() + dfk.bytes() + bgm.bytes() + rc_scratch.bytes() + rc_block.bytes() + Adf.bytes() +
+                   Bdf.bytes() + Xdf.bytes() + Rdf.bytes() + U.bytes() + Lam.bytes() + Brhs.bytes() + R.bytes() +
+                   Bc.bytes() + Xc.bytes() + v32.bytes() + x32.bytes() + r32.bytes() + dscratch.bytes() +
+                   rx_dof_d.bytes() + tx_dof_d.bytes() + rx_sign_d.bytes() + tx_sign_d.bytes() + cur_d.bytes() +
+                   S_d.bytes() + Smeas_d.bytes() + r_d.bytes() + grad_d.bytes() + w_d.bytes() + J_d.bytes();
+        for (int k = 0; k < 2; ++k) b += sch64[k].bytes() + sch32[k].bytes();
+        return b;
+    }
 };
 
 namespace {
@@ -1371,6 +1384,13 @@ mwi_status mwi_oras_traffic(mwi_problem_t P, int32_t m, double* bytes) {
         }
         const double n = (double)P->mesh->T.ndof, nloc = (double)D.sub_off[D.n_sub];
         *bytes = factor * e + (rows + 2.0 * (n + nloc)) * m * e;  // + gather and scatter
+    });
+}
+
+mwi_status mwi_problem_device_bytes(mwi_problem_t P, int64_t* bytes) {
+    return guard([&] {
+        MWI_REQUIRE(P && bytes, MWI_EINVAL, "null argument");
+        *bytes = (int64_t)P->device_bytes();
     });
 }
 

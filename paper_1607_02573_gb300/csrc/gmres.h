@@ -39,6 +39,10 @@ struct Gmres {
               int self = 0);
     void column_norms2(const C* x, double* out, cudaStream_t st);
     void column_norms2_into(const C* x, double* out, double2* tmp, cudaStream_t st);
+    size_t bytes() const {
+        return V.bytes() + Z.bytes() + W.bytes() + H.bytes() + cs.bytes() + sn.bytes() + g.bytes() + y.bytes() +
+               h.bytes() + hacc.bytes() + partial.bytes() + dvec.bytes() + ivec.bytes();
+    }
 };
 
 // FGMRES whose FP64-quality vectors (basis V, w, residual, iterate) are
@@ -70,6 +74,11 @@ struct GmresDF {
               cudaStream_t st, int* iters_used);
     // ||x_c||^2 from the FP32 head plane
     void norms2(const float2* xh, double* out, cudaStream_t st);
+    size_t bytes() const {
+        return V.bytes() + Z.bytes() + W.bytes() + hdf.bytes() + hdf2.bytes() + scal.bytes() + ydf.bytes() +
+               invdf.bytes() + H.bytes() + Hp.bytes() + cs.bytes() + sn.bytes() + g.bytes() + y.bytes() + h.bytes() +
+               partial.bytes() + dvec.bytes() + ivec.bytes();
+    }
 };
 
 // True block flexible GMRES over complex FP64 [n][m] blocks: one Krylov space
@@ -92,6 +101,9 @@ struct BlockGmres {
     void block_update(double2* out, const double2* in, int nq, const double2* Cm, double alpha, double beta,
                       cudaStream_t st);
     int chol_qr(double2* X, std::vector<std::complex<double>>& S, cudaStream_t st);
+    size_t bytes() const {
+        return V.bytes() + Z.bytes() + W.bytes() + coef.bytes() + small.bytes() + partial.bytes();
+    }
 };
 
 // w = A z with A as double-float planes (hi nnz entries, then lo), z complex FP32

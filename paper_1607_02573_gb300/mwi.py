@@ -77,6 +77,7 @@ _SIGS = {
     "mwi_matrix_csr": [_vp, _i64p, _i64p, _i32p, _dp],
     "mwi_decomposition": [_vp, _i32p, _i64p],
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
+    "mwi_problem_device_bytes": [_vp, _i64p],
     "mwi_oras_traffic": [_vp, C.c_int32, _dp],
     "mwi_p1_tet_eps": [_vp, _vp, _vp, _vp],
     "mwi_p1_gradient": [_vp, _vp, _vp, C.c_double, _vp, _dp, _vp],
@@ -322,6 +323,12 @@ class Problem:
         d = C.c_double()
         check(mwi_factor_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         return dict(factor_entries=a.value, n_fronts=b.value, max_front=c.value, factor_flops=d.value)
+
+    def device_bytes(self):
+        """Device bytes held by this problem (the mesh's shared structures excluded)."""
+        b = C.c_int64()
+        check(mwi_problem_device_bytes(self.h, C.byref(b)))
+        return b.value
 
     def oras_traffic(self, m):
         """Algorithmic bytes of one ORAS application to m columns."""
