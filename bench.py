@@ -45,8 +45,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--nested-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--nested-steps", type=int, default=3)
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="time the mixed arm alone (no other arms, no CPU baseline, 2 e2e requests): for profiling")
+    ap.add_argument("--solve", default=None,
+                    help="one forward solve instead of the gradient step, for sizing and profiling: "
+                         "NXY,NZ,N_SUB,PRECISION[,N_ANT,ORDER,RINGS,MAX_BLOCK,RESTART] "
+                         "(defaults 30,28,32,1,32,1,1,64,50: 120,288 tets; RINGS=5 is the 160-antenna layout)")
     ap.add_argument("--nxy", type=int, default=45)
     ap.add_argument("--nz", type=int, default=42)
     ap.add_argument("--n-ant", type=int, default=32)
@@ -61,6 +67,8 @@ def parse():
                     help="timed gradient steps with Krylov recycling across steps (0: skip)")
     ap.add_argument("--block-steps", type=int, default=1,
                     help="timed forward solves comparing true block FGMRES with pseudo-block (0: skip)")
+    ap.add_argument("--p1-steps", type=int, default=2,
+                    help="timed gradient steps with the nodal (P1) parameter (0: skip)")
     ap.add_argument("--engine", type=int, default=2, help="complex FP32 sweep engine (see mwi_solver_opts)")
     ap.add_argument("--requests", type=int, default=200,
                     help="end-to-end gradient requests (host in, host out) for e2e throughput and p50/p99 latency")
@@ -157,6 +165,7 @@ def run_mine(args, rank, world):
                         factor_reuse=factor_reuse)
         fs = P.factor_stats()
         fs["oras_bytes_per_call"] = P.oras_traffic(min(32, args.n_ant))
+        fs["nloc"] = int(P.decomposition(64)[1].sum())
         # synthetic measurements: S of the two-inclusion target map plus 1 % noise
         from synthetic import add_noise, chamber_target_eps
         P.update_eps(torch.from_numpy(chamber_target_eps(mesh.xyz, mesh.tet)).to(dev))
@@ -231,6 +240,10 @@ def run_mine(args, rank, world):
         P.close()
         return res
 
+    if args.only_mixed:
+        args.nested_steps = args.fp64_steps = args.recycle_steps = args.block_steps = args.p1_steps = 0
+        args.requests = 2
+        args.no_cpu_baseline = True
     results["mixed"] = one_arm(1, args.steps, args.warmup, max(2, args.requests))
     results["nested"] = one_arm(2, args.nested_steps, args.warmup, 0) if args.nested_steps > 0 else None
     results["fp64"] = one_arm(0, args.fp64_steps, args.warmup, 0) if args.fp64_steps > 0 else None
@@ -266,51 +279,75 @@ def run_mine(args, rank, world):
                 "kernel_ms": {k: round(v / args.block_steps, 2) for k, v in
                               zip(["spmm", "oras_apply", "orthogonalisation"], kms[:3].tolist())}}
             P.close()
-    # nodal (P1) parameter with the gradient penalty: the two kernels a P1
-    # objective adds to a gradient step (centroid sampling, spreading + penalty)
-    with torch.cuda.stream(stream):
-        kap = torch.full((mesh.nv,), 44 - 20j, dtype=torch.complex128, device=dev)
-        kap += torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, mesh.nv)).to(dev)
-        g_t = torch.from_numpy(np.random.default_rng(4).standard_normal(mesh.nt) + 0j).to(dev)
-        for _ in range(3):
-            M.p1_tet_eps(kap, stream)
-            M.p1_gradient(g_t, kap, 1e-3, stream)
-        reps = 50
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        for _ in range(reps):
-            M.p1_tet_eps(kap, stream)
-        e1.record(stream)
-        for _ in range(reps):
-            M.p1_gradient(g_t, kap, 1e-3, stream)
-        e2.record(stream)
+    # nodal (P1) parameter with the gradient penalty (kappa varying inside every
+    # tet): the same gradient step with the vertex parameter, mixed path
+    if args.p1_steps > 0:
+        P = mwi.Problem(M, eps_d, FREQ, stream=stream, n_sub=64, precision=1, rtol=RTOL, max_iter=500,
+                        nd_leaf=args.nd_leaf, sweep_engine=args.engine)
+        with torch.cuda.stream(stream):
+            kap = torch.full((mesh.nv,), 44 - 20j, dtype=torch.complex128, device=dev)
+            kap += torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, mesh.nv)).to(dev)
+        S_meas = P.forward_solve(ants, ants) * 1.01
+        w = mwi.normalised_weights(S_meas)
+
+        def p1_step():
+            P.update_kappa(kap)
+            P.forward_solve(ants, ants)
+            return P.misfit_and_gradient_kappa(S_meas, w, 1e-3)
+
+        p1_step()
         torch.cuda.synchronize()
-        results["p1"] = {"tet_eps_ms": e0.elapsed_time(e1) / reps, "gradient_and_penalty_ms": e1.elapsed_time(e2) / reps,
-                         "nv": int(mesh.nv), "what": "per call, including the penalty read-back to the host"}
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        for _ in range(args.p1_steps):
+            J, R, _ = p1_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / args.p1_steps
+        results["p1"] = {"ms_per_step": pms, "value": 2 * ants.shape[0] / (pms / 1e3), "unit": UNIT,
+                         "nv": int(mesh.nv), "steps": args.p1_steps, "J": J, "R": R,
+                         "what": "gradient step with the nodal parameter (vertex-weighted mass term, "
+                                 "normalised misfit, gradient penalty alpha = 1e-3): update_kappa (P1 masses, "
+                                 "assembly, factorisation), forward and adjoint solves, vertex gradient"}
+        P.close()
     return mesh, M, results
 
 
-def roofline(res, ndof, m):
-    """ORAS apply (gather, forward and backward multifrontal sweeps, scatter):
-    HBM-bound -- each stored factor entry is read once per sweep and the local
-    vectors move a fixed number of times per front (the library's algorithmic
-    byte count, mwi_oras_traffic); achieved = those bytes / the measured time
-    per call, against the measured copy bandwidth."""
+def roofline(res, ndof, m, traffic=None):
+    """ORAS apply (gather, forward and backward multifrontal sweeps, scatter),
+    HBM-bound.  Algorithmic bytes per call, each operand moved once: the
+    complex FP32 factors (every stored panel entry and D^-1 once) plus the
+    input and output vectors, n x m complex FP32 each; achieved = those bytes
+    / the measured time per call (CUDA events on the problem's stream around
+    every call in the timed region), against the measured copy bandwidth.
+    The library's own count of what the sweeps must move (factors once per
+    sweep, the local and update vectors of every front: mwi_oras_traffic) is
+    reported beside it as frac_impl_traffic."""
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     calls = res["kernel_calls"][1]
     if calls == 0:
         return None
     per_call_ms = res["kernel_ms"][1] / calls
-    nbytes = res["factor"]["oras_bytes_per_call"]
-    achieved = nbytes / (per_call_ms / 1e3) / 1e9
+    fac = res["factor"]
+    alg = (fac["factor_entries"] + fac["nloc"]) * 8.0 + 2.0 * ndof * m * 8.0
+    impl = fac["oras_bytes_per_call"]
+    achieved = alg / (per_call_ms / 1e3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
-    src = "measured copy bandwidth (hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
-    flops = 2.0 * 8.0 * res["factor"]["factor_entries"] * m
-    return {"bound": "hbm", "kernel": "ORAS apply (c64 multifrontal fwd/bwd sweeps on TF32 tensor cores)",
-            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": None, "peak_source": src, "algorithmic_bytes_per_call": nbytes,
-            "ms_per_call": per_call_ms, "tensor_tflops": round(flops / (per_call_ms / 1e3) / 1e12, 2)}
+    src = "measured copy bandwidth (hbm_gbs) of MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    flops = 2.0 * 8.0 * fac["factor_entries"] * m
+    out = {"bound": "hbm", "kernel": "ORAS apply (c64 multifrontal forward/backward sweeps, gather, scatter)",
+           "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+           "traffic": None, "peak_source": src, "algorithmic_bytes_per_call": alg,
+           "what_algorithmic": "c64 factor entries (panels + D^-1) once + x in + y out (n x m c64 each)",
+           "impl_bytes_per_call": impl,
+           "frac_impl_traffic": round(impl / (per_call_ms / 1e3) / 1e9 / peak, 4),
+           "ms_per_call": per_call_ms, "tensor_tflops": round(flops / (per_call_ms / 1e3) / 1e12, 2)}
+    if traffic:
+        out["traffic"] = traffic["bytes_per_call"]
+        out["traffic_source"] = traffic["source"]
+        out["traffic_over_algorithmic"] = round(traffic["bytes_per_call"] / alg, 3)
+    return out
 
 
 def cpu_baseline(args, steps=1):
@@ -403,6 +440,47 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def run_solve(args):
+    """One forward solve of a chamber (--solve): one JSON line with the sizes,
+    the setup and solve times, the solver statistics and S's reciprocity."""
+    import torch
+
+    from paper_1607_02573_gb300 import mwi
+    from synthetic import antenna_array, chamber_eps, chamber_mesh, ring_antennas
+
+    vals = [int(v) for v in args.solve.split(",")]
+    nxy, nz, n_sub, prec, n_ant, order, rings, max_block, restart = (vals + [30, 28, 32, 1, 32, 1, 1, 64, 50][
+        len(vals):])[:9]
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    mesh = chamber_mesh(nxy, nz)
+    eps = chamber_eps(mesh.xyz, mesh.tet)
+    zs = [0.14] if rings == 1 else [0.06, 0.10, 0.14, 0.18, 0.22]
+    ants = antenna_array([a for z in zs for a in ring_antennas(n_ant, z=z)])
+    M = mwi.Mesh(mesh.xyz, mesh.tet, mesh.bface_tag, order=order)
+    t1 = time.time()
+    P = mwi.Problem(M, eps, FREQ, n_sub=n_sub, precision=prec, rtol=RTOL, max_block=max_block, restart=restart,
+                    sweep_engine=args.engine, verbose=2)
+    t2 = time.time()
+    S = P.forward_solve(ants, ants, allow_notconv=True)
+    torch.cuda.synchronize()
+    t3 = time.time()
+    kms, kcnt = P.kernel_times(reset=True)
+    info = P.info.as_dict()
+    line = {"mode": "solve", "tets": int(mesh.nt), "dof": int(M.ndof), "order": order, "columns": int(ants.shape[0]),
+            "n_sub": n_sub, "precision": prec, "engine": args.engine, "mesh_s": round(t1 - t0, 2),
+            "setup_s": round(t2 - t1, 2), "forward_s": round(t3 - t2, 3),
+            "rhs_solves_per_s": round(ants.shape[0] / (t3 - t2), 2), "factor": P.factor_stats(),
+            "oras_impl_bytes_per_call": P.oras_traffic(min(32, ants.shape[0])), "solve": info,
+            "kernel_ms": dict(zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"],
+                                  [round(v, 2) for v in kms.tolist()])),
+            "kernel_calls": kcnt.tolist(),
+            "reciprocity": float(np.linalg.norm(S - S.T) / np.linalg.norm(S))}
+    P.close()
+    M.close()
+    print(json.dumps(line))
+
+
 def max_over_ranks(value, world, device="cpu"):
     """The largest value over all ranks (a job's time is its slowest rank's);
     every rank gets it.  The process group must be initialised when world > 1."""
@@ -449,6 +527,10 @@ def main():
     if args.serve > 0:
         if rank == 0:
             run_serving(args)
+        return
+    if args.solve:
+        if rank == 0:
+            run_solve(args)
         return
     import torch
     if world > 1:

@@ -273,25 +273,49 @@ mwi_status mwi_decomposition(mwi_problem_t prob, int32_t* part, int64_t* n_local
 mwi_status mwi_factor_stats(mwi_problem_t prob, int64_t* factor_entries, int64_t* n_fronts,
                             int64_t* max_front, double* factor_flops);
 
-/* Nodal (P1) permittivity parameter (the P1 parameter of Section 6.3).
- * Per-tet relative permittivity from per-vertex values kappa_dev [nv] (complex,
- * interleaved; the caller's vertex numbering): eps_t = (1/4) sum of kappa over
- * the tet's vertices, i.e. the P1 field at the tet's centroid, written to
- * eps_dev [nt] (device, the layout mwi_update_eps_device reads).  Enqueued on
- * `stream`; no synchronisation. */
-mwi_status mwi_p1_tet_eps(mwi_mesh_t mesh, const double* kappa_dev, double* eps_dev, void* stream);
+/* Nodal (P1) permittivity parameter (Section 6.3: a piecewise-linear parameter
+ * on the state mesh).  kappa_dev [nv] (device, interleaved complex, the
+ * caller's vertex numbering) holds a relative permittivity per vertex; the
+ * field kappa(x) = sum_v kappa_v lambda_v(x) varies inside every tet, so the
+ * mass term of Eq. pbdirectvarf becomes
+ *     int_t kappa N_i . N_j = sum_w kappa_{v_w} int_t lambda_w N_i . N_j
+ * (four vertex-weighted element masses per tet, closed forms, built on the
+ * mesh's first use of this call and kept with the mesh).  beta on impedance
+ * faces and the interface wavenumber of the ORAS local problems take the P1
+ * field at the owning tet's centroid, 1/4 sum of its vertex values (the paper
+ * does not say; this is the library's reading).  Reassembles A and, as
+ * mwi_update_eps does (including opts.factor_reuse), the subdomain factors.
+ * Until the next mwi_update_eps[_device] the problem is in nodal-parameter
+ * mode: mwi_misfit_and_gradient[_device] return MWI_ESTATE and
+ * mwi_misfit_and_gradient_kappa_device gives the gradient.  Errors:
+ * MWI_EINVAL for a null pointer or a non-finite kappa (checked on the device
+ * before anything changes). */
+mwi_status mwi_update_kappa_device(mwi_problem_t prob, const double* kappa_dev);
 
-/* Gradient of Phi(kappa) = J(eps(kappa)) + R(kappa) with respect to the nodal
- * parameter, R = (alpha/2) integral |grad kappa|^2 = (alpha/2) Re(kappa^H K kappa)
- * (the gradient penalty of Eq. defJ2; K the P1 stiffness matrix of the mesh,
- * built on the first call).  grad_tet_dev [nt]: the per-tet gradient of J as
- * mwi_misfit_and_gradient_device returns it (dJ/dRe eps_t + i dJ/dIm eps_t);
- * grad_vertex_dev [nv] receives 1/4 sum over the vertex's tets of grad_tet plus
- * alpha (K kappa)_v, in the same convention.  penalty (host, may be NULL): R;
- * when given, the call synchronises `stream`.  Errors: MWI_EINVAL for null
- * pointers or alpha < 0. */
-mwi_status mwi_p1_gradient(mwi_mesh_t mesh, const double* grad_tet_dev, const double* kappa_dev, double alpha,
-                           double* grad_vertex_dev, double* penalty, void* stream);
+/* Objective of Eq. defJ2 for the nodal parameter: J = 1/2 sum_ij w_ij
+ * |S_ij - S_meas_ij|^2 (w_dev nullable: w = 1; the normalised misfit takes
+ * w_ij = 1/|S_empty_ij|^2, see mwi_normalised_weights) for the S of the last
+ * forward solve, and the penalty R = (alpha/2) int |grad kappa|^2 =
+ * (alpha/2) Re(kappa^H K kappa) (K the P1 stiffness matrix).  Runs the adjoint
+ * solve (Eq. pbadj) with the same factors and writes to dPhi_dkappa_dev [nv]
+ * (device, interleaved) the gradient of J + R with respect to the vertex
+ * values, dPhi/dRe kappa_v + i dPhi/dIm kappa_v: per (tet, vertex) the term
+ * k0^2 sum_j lambda_j^T M_t^(w) u_j plus a quarter of the tet's beta term,
+ * conjugated and summed over the vertex's tets (ascending), plus
+ * alpha (K kappa)_v.  J_out and R_out (nullable) are host scalars; S_meas_dev
+ * and w_dev are [n_rx*n_tx] column-major device arrays.  MWI_ESTATE without
+ * a prior mwi_update_kappa_device and forward solve; MWI_EINVAL for alpha < 0;
+ * MWI_ENOTCONV still fills every output. */
+mwi_status mwi_misfit_and_gradient_kappa_device(mwi_problem_t prob, const double* S_meas_dev,
+                                                const double* w_dev, double alpha, double* J_out,
+                                                double* R_out, double* dPhi_dkappa_dev,
+                                                mwi_solve_info* info);
+
+/* Weights of the normalised misfit of Eq. defJ2: w[e] = 1 / |S_empty[e]|^2
+ * for count complex entries (host arrays; S_empty interleaved, as
+ * mwi_forward_solve returns it for the empty -- gel-filled -- chamber).
+ * MWI_EINVAL if an entry is zero or not finite. */
+mwi_status mwi_normalised_weights(const double* S_empty, int64_t count, double* w_out);
 
 /* Algorithmic memory traffic of one ORAS application (Eq. ORAS) to m columns,
  * in bytes, for the roofline of the sweeps (no counterpart in the paper; a
@@ -319,6 +343,11 @@ mwi_status mwi_kernel_times(mwi_problem_t prob, double* ms, int64_t* counts, int
 
 /* Number of kernels this library has launched in the process so far. */
 int64_t mwi_launch_count(void);
+
+/* Number of device allocations (cudaMalloc calls) this library has made in
+ * the process so far, successful or not; lets a caller check that a call
+ * allocated nothing. */
+int64_t mwi_device_alloc_count(void);
 
 #ifdef __cplusplus
 }

@@ -69,21 +69,19 @@ def lbfgs_invert(problem, eps0, tx, rx, S_meas, w=None, iters=10, lr=1.0, histor
 
 def normalised_weights(problem, eps_empty, tx, rx):
     """Weights w_ij = 1 / |S^empty_ij|^2 of the normalised misfit (Eq. defJ2),
-    from one forward solve of the empty (gel-filled) chamber eps_empty [nt]."""
+    from one forward solve of the empty (gel-filled) chamber eps_empty [nt];
+    the library forms them (mwi_normalised_weights)."""
+    from . import mwi
     problem.update_eps(eps_empty)
-    S = problem.forward_solve(tx, rx)
-    return 1.0 / np.abs(S) ** 2
+    return mwi.normalised_weights(problem.forward_solve(tx, rx))
 
 
 def p1_objective(problem, kappa, tx, rx, S_meas, w=None, alpha=0.0):
-    """Phi(kappa) = J(eps(kappa)) + (alpha/2) integral |grad kappa|^2 for a
-    per-vertex permittivity kappa (device tensor [nv], the P1 parameter of
-    Section 6.3; eps_t is the P1 field at the tet centroid), with its gradient
-    dPhi/dRe kappa + i dPhi/dIm kappa as a device tensor [nv]."""
-    mesh = problem.mesh
-    eps = mesh.p1_tet_eps(kappa, problem.stream)
-    problem.update_eps(eps)
+    """Phi(kappa) = J(kappa) + (alpha/2) integral |grad kappa|^2 (Eq. defJ2) for a
+    per-vertex permittivity kappa (device tensor [nv]; the piecewise-linear
+    parameter of Section 6.3, varying inside every tet in the mass term), with
+    its gradient dPhi/dRe kappa + i dPhi/dIm kappa as a device tensor [nv]."""
+    problem.update_kappa(kappa)
     problem.forward_solve(tx, rx)
-    J, g_t = problem.misfit_and_gradient_device(S_meas, w)
-    g_v, R = mesh.p1_gradient(g_t, kappa, alpha, problem.stream)
-    return J + R, g_v
+    J, R, g = problem.misfit_and_gradient_kappa(S_meas, w, alpha)
+    return J + R, g

@@ -19,6 +19,7 @@ namespace mwi {
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_device_allocs{0};
 
 static const double kPi = 3.14159265358979323846;
 static const double kC0 = 299792458.0;
@@ -96,11 +97,11 @@ struct mwi_mesh {
     DevBuf<int32_t> A_fu_face, A_fu_tet;
     std::vector<std::shared_ptr<DecompEntry>> cache;
     std::mutex mu;
-    // nodal (P1) parameter: vertex -> tets, P1 stiffness, block partial sums (built on first use)
+    // nodal (P1) parameter: vertex -> tets, P1 stiffness, vertex-weighted element
+    // masses (built on first use)
     bool have_p1 = false;
     DevBuf<int32_t> v2t_ptr, v2t, p1_rp, p1_col;
-    DevBuf<double> p1_val, p1_partial;
-    std::vector<double> p1_partial_host;
+    DevBuf<double> p1_val, Mv;
 };
 
 struct mwi_problem {
@@ -128,6 +129,14 @@ struct mwi_problem {
     int rec_dropped = 0;
     DevBuf<double2> rc_scratch, rc_block;
     int reuse_count = 0;  // eps_r updates since the factors were computed
+    // nodal parameter (mwi_update_kappa_device): kappa per vertex, the per-tet
+    // complex masses sum_w kappa_w M_t^(w) used by the assembly, the (tet,
+    // vertex) gradient terms and the penalty's block sums
+    bool p1 = false;
+    DevBuf<double2> kappa, Mk, grad_tw;
+    DevBuf<double> p1_partial;
+    std::vector<double> p1_partial_host;
+    DevBuf<int> nonfinite;
     DevBuf<float2> Adf, Bdf, Xdf, Rdf;   // double-float planes
     DevBuf<double2> U, Lam, Brhs, R, Bc, Xc;
     DevBuf<float2> v32, x32, r32;
@@ -163,7 +172,8 @@ struct mwi_problem {
                    Bdf.bytes() + Xdf.bytes() + Rdf.bytes() + U.bytes() + Lam.bytes() + Brhs.bytes() + R.bytes() +
                    Bc.bytes() + Xc.bytes() + v32.bytes() + x32.bytes() + r32.bytes() + dscratch.bytes() +
                    rx_dof_d.bytes() + tx_dof_d.bytes() + rx_sign_d.bytes() + tx_sign_d.bytes() + cur_d.bytes() +
-                   S_d.bytes() + Smeas_d.bytes() + r_d.bytes() + grad_d.bytes() + w_d.bytes() + J_d.bytes();
+                   S_d.bytes() + Smeas_d.bytes() + r_d.bytes() + grad_d.bytes() + w_d.bytes() + J_d.bytes() +
+                   kappa.bytes() + Mk.bytes() + grad_tw.bytes() + p1_partial.bytes() + nonfinite.bytes();
         for (int k = 0; k < 2; ++k) b += sch64[k].bytes() + sch32[k].bytes();
         return b;
     }
@@ -256,6 +266,17 @@ void harvest_events(mwi_problem* P) {
     P->ev_used.clear();
 }
 
+// finiteness of a complex device array (host arrays are checked on the host)
+void check_finite_device(mwi_problem* P, const double2* x, int64_t n, const char* what) {
+    P->nonfinite.ensure(1);
+    MWI_CUDA(cudaMemsetAsync(P->nonfinite.p, 0, sizeof(int), P->st));
+    launch_count_nonfinite(n, x, P->nonfinite.p, P->st);
+    int bad = 0;
+    MWI_CUDA(cudaMemcpyAsync(&bad, P->nonfinite.p, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+    MWI_CUDA(cudaStreamSynchronize(P->st));
+    MWI_REQUIRE(bad == 0, MWI_EINVAL, std::string(what) + " not finite (" + std::to_string(bad) + " entries)");
+}
+
 void build_mesh_device(mwi_mesh* M) {
     Topology& T = M->T;
     cudaStream_t st = M->st;
@@ -274,6 +295,7 @@ void build_mesh_device(mwi_mesh* M) {
     M->tabs.nlf = tab.nlf;
     M->tabs.npack_f = tab.npack_f;
     up(M->tabs.m_terms, tab.m_terms, st);
+    up(M->tabs.mv_c, tab.mv_c, st);
     up(M->tabs.m_ptr, tab.m_ptr, st);
     up(M->tabs.k_terms, tab.k_terms, st);
     up(M->tabs.k_ptr, tab.k_ptr, st);
@@ -482,8 +504,9 @@ void numeric_setup(mwi_problem* P, bool refactor = true) {
     const bool mixed = P->opts.precision != 0;
     const bool nested = P->opts.precision == 2;
     if (nested) P->Aval32.ensure(M->A.nnz);
+    const double2* Mk = P->p1 ? P->Mk.p : nullptr;
     launch_slot_fill(M->A, M->Kp.p, M->Mp.p, M->tabs.npack, M->Bf.p, M->tabs.npack_f, M->A_fu_face.p, P->A_coef.p,
-                     P->eps.p, P->k0, P->Aval.p, nested ? P->Aval32.p : nullptr, st);
+                     P->eps.p, P->k0, P->Aval.p, nested ? P->Aval32.p : nullptr, st, Mk);
     if (mixed && !nested) {
         P->Adf.ensure(2 * (size_t)M->A.nnz);
         split_c128(M->A.nnz, P->Aval.p, P->Adf.p, st);
@@ -498,7 +521,7 @@ void numeric_setup(mwi_problem* P, bool refactor = true) {
     launch_face_coef(E.fu_tet.p, (int64_t)E.D.B_faces.face.size(), P->eps.p, P->k0, P->B_coef.p, st);
     P->Bval.ensure(E.B.nnz);
     launch_slot_fill(E.B, M->Kp.p, M->Mp.p, M->tabs.npack, M->Bf.p, M->tabs.npack_f, E.fu_face.p, P->B_coef.p,
-                     P->eps.p, P->k0, P->Bval.p, nullptr, st);
+                     P->eps.p, P->k0, P->Bval.p, nullptr, st, Mk);
     P->perturbed.ensure(1);
     MWI_CUDA(cudaMemsetAsync(P->perturbed.p, 0, sizeof(int), st));
     if (mixed) {
@@ -551,6 +574,7 @@ void create_problem(mwi_mesh* M, const double* eps, bool eps_dev, double freq, c
     }
     P->eps.alloc(M->T.nt);
     if (eps_dev) {
+        check_finite_device(P.get(), reinterpret_cast<const double2*>(eps), M->T.nt, "eps_r");
         MWI_CUDA(cudaMemcpyAsync(P->eps.p, eps, M->T.nt * sizeof(double2), cudaMemcpyDeviceToDevice, P->st));
     } else {
         for (int64_t t = 0; t < M->T.nt; ++t)
@@ -1044,20 +1068,28 @@ mwi_status mwi_assemble_device(mwi_mesh_t mesh, const double* eps_r_dev, double 
     return guard([&] { create_problem(mesh, eps_r_dev, true, freq_hz, opts, cuda_stream, out); });
 }
 
+// reassemble for the current parameter; factor reuse: up to factor_reuse
+// consecutive updates keep the factors
+static void refresh_operator(mwi_problem_t P) {
+    const bool refactor = P->opts.factor_reuse <= 0 || P->reuse_count >= P->opts.factor_reuse;
+    numeric_setup(P, refactor);
+    P->reuse_count = refactor ? 0 : P->reuse_count + 1;
+    P->have_fwd = false;
+    P->have_adj = false;
+}
+
 static void update_eps(mwi_problem_t P, const double* eps, bool dev) {
     MWI_REQUIRE(P && eps, MWI_EINVAL, "null argument");
     const int64_t nt = P->mesh->T.nt;
     if (!dev)
         for (int64_t t = 0; t < nt; ++t)
             MWI_REQUIRE(std::isfinite(eps[2 * t]) && std::isfinite(eps[2 * t + 1]), MWI_EINVAL, "eps_r not finite");
+    else
+        check_finite_device(P, reinterpret_cast<const double2*>(eps), nt, "eps_r");
     MWI_CUDA(cudaMemcpyAsync(P->eps.p, eps, nt * sizeof(double2),
                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, P->st));
-    // factor reuse: up to factor_reuse consecutive updates keep the factors
-    const bool refactor = P->opts.factor_reuse <= 0 || P->reuse_count >= P->opts.factor_reuse;
-    numeric_setup(P, refactor);
-    P->reuse_count = refactor ? 0 : P->reuse_count + 1;
-    P->have_fwd = false;
-    P->have_adj = false;
+    P->p1 = false;
+    refresh_operator(P);
 }
 
 mwi_status mwi_update_eps(mwi_problem_t prob, const double* eps_r) {
@@ -1112,55 +1144,68 @@ mwi_status mwi_forward_solve(mwi_problem_t P, const mwi_antenna* tx, int32_t n_t
     return g != MWI_OK ? g : status;
 }
 
+// misfit J and r = S - S_meas (Eq. defJ) for the last forward solve, the
+// adjoint sources (Eq. pbadj) and the adjoint solve with the same factors;
+// J stays on the device (P->J_d).  MWI_ENOTCONV of the adjoint solve is
+// returned in status, not thrown.
+static void misfit_and_adjoint(mwi_problem_t P, const double* S_meas, const double* w, bool dev,
+                               mwi_solve_info* info, mwi_status& status) {
+    MWI_REQUIRE(P->have_fwd, MWI_ESTATE, "misfit_and_gradient needs a prior forward_solve");
+    const Topology& T = P->mesh->T;
+    cudaStream_t st = P->st;
+    const int m = P->m_fwd, n_rx = P->n_rx;
+    const int cnt = n_rx * m;
+    const int64_t nm = T.ndof * (int64_t)m;
+    const auto kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    P->Smeas_d.ensure(cnt);
+    P->r_d.ensure(cnt);
+    P->J_d.ensure(1);
+    MWI_CUDA(cudaMemcpyAsync(P->Smeas_d.p, S_meas, cnt * sizeof(double2), kind, st));
+    const double* wd = nullptr;
+    if (w) {
+        P->w_d.ensure(cnt);
+        MWI_CUDA(cudaMemcpyAsync(P->w_d.p, w, cnt * sizeof(double), kind, st));
+        wd = P->w_d.p;
+    }
+    launch_misfit(cnt, P->S_d.p, P->Smeas_d.p, wd, P->r_d.p, P->J_d.p, st);
+    P->Brhs.ensure(nm);
+    MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));
+    launch_adjoint_rhs(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->r_d.p, wd, P->Brhs.p, st);
+    P->Lam.ensure(nm);
+    // recycled space of the adjoint solve: the previous adjoint solutions and
+    // the current forward solutions (whose span holds the adjoint solution
+    // exactly when the receivers are among the transmitters)
+    const bool rec = P->opts.recycle && P->rec_m[1] == m;
+    const double2* fwd = P->opts.recycle && P->rec_m[0] == m ? P->U.p : nullptr;
+    P->rec_m[1] = 0;
+    try {
+        solve_columns(P, P->Brhs.p, P->Lam.p, m, info, rec, fwd);
+        P->rec_m[1] = m;
+    } catch (const Error& e) {
+        if (e.status != MWI_ENOTCONV) throw;
+        status = MWI_ENOTCONV;
+        set_last_error(e.what());
+    }
+}
+
 static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const double* w, double* J_out,
                                    double* dJ, mwi_solve_info* info, bool dev) {
     mwi_status status = MWI_OK;
     mwi_status g = guard([&] {
         MWI_REQUIRE(P && S_meas && J_out && dJ, MWI_EINVAL, "null argument");
-        MWI_REQUIRE(P->have_fwd, MWI_ESTATE, "misfit_and_gradient needs a prior forward_solve");
+        MWI_REQUIRE(!P->p1, MWI_ESTATE, "the operator holds a nodal parameter: use "
+                                        "mwi_misfit_and_gradient_kappa_device");
+        misfit_and_adjoint(P, S_meas, w, dev, info, status);
         const Topology& T = P->mesh->T;
         cudaStream_t st = P->st;
-        const int m = P->m_fwd, n_rx = P->n_rx;
-        const int cnt = n_rx * m;
-        const int64_t nm = T.ndof * (int64_t)m;
-        const auto kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        P->Smeas_d.ensure(cnt);
-        P->r_d.ensure(cnt);
-        P->J_d.ensure(1);
-        MWI_CUDA(cudaMemcpyAsync(P->Smeas_d.p, S_meas, cnt * sizeof(double2), kind, st));
-        const double* wd = nullptr;
-        if (w) {
-            P->w_d.ensure(cnt);
-            MWI_CUDA(cudaMemcpyAsync(P->w_d.p, w, cnt * sizeof(double), kind, st));
-            wd = P->w_d.p;
-        }
-        launch_misfit(cnt, P->S_d.p, P->Smeas_d.p, wd, P->r_d.p, P->J_d.p, st);
-        P->Brhs.ensure(nm);
-        MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));
-        launch_adjoint_rhs(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->r_d.p, wd, P->Brhs.p, st);
-        P->Lam.ensure(nm);
-        // recycled space of the adjoint solve: the previous adjoint solutions and
-        // the current forward solutions (whose span holds the adjoint solution
-        // exactly when the receivers are among the transmitters)
-        const bool rec = P->opts.recycle && P->rec_m[1] == m;
-        const double2* fwd = P->opts.recycle && P->rec_m[0] == m ? P->U.p : nullptr;
-        P->rec_m[1] = 0;
-        try {
-            solve_columns(P, P->Brhs.p, P->Lam.p, m, info, rec, fwd);
-            P->rec_m[1] = m;
-        } catch (const Error& e) {
-            if (e.status != MWI_ENOTCONV) throw;
-            status = MWI_ENOTCONV;
-            set_last_error(e.what());
-        }
         double2* out = dev ? reinterpret_cast<double2*>(dJ) : nullptr;
         if (!dev) {
             P->grad_d.ensure(T.nt);
             out = P->grad_d.p;
         }
         mwi_mesh* M = P->mesh;
-        launch_gradient(T.order, T.nt, m, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p, M->face_dofs.p, M->Mp.p,
-                        M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, out, st);
+        launch_gradient(T.order, T.nt, P->m_fwd, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p, M->face_dofs.p,
+                        M->Mp.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, out, st);
         MWI_CUDA(cudaMemcpyAsync(J_out, P->J_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         if (!dev)
             MWI_CUDA(cudaMemcpyAsync(dJ, P->grad_d.p, T.nt * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -1330,39 +1375,74 @@ static void ensure_p1(mwi_mesh* M) {
     up(M->p1_rp, rp, M->st);
     up(M->p1_col, col, M->st);
     up(M->p1_val, val, M->st);
-    M->p1_partial.alloc((size_t)p1_gradient_blocks(T.nv));
-    M->p1_partial_host.assign((size_t)p1_gradient_blocks(T.nv), 0.0);
+    M->Mv.alloc((size_t)T.nt * 4 * M->tabs.npack);
+    launch_elem_vertex_mass(M->xyz.p, M->tv.p, T.nt, M->tabs, M->Mv.p, M->st);
     MWI_CUDA(cudaStreamSynchronize(M->st));
     M->have_p1 = true;
 }
 
-mwi_status mwi_p1_tet_eps(mwi_mesh_t M, const double* kappa_dev, double* eps_dev, void* stream) {
+mwi_status mwi_update_kappa_device(mwi_problem_t P, const double* kappa_dev) {
     return guard([&] {
-        MWI_REQUIRE(M && kappa_dev && eps_dev, MWI_EINVAL, "null argument");
-        launch_p1_tet_eps(M->T.nt, M->tv.p, (const double2*)kappa_dev, (double2*)eps_dev, (cudaStream_t)stream);
+        MWI_REQUIRE(P && kappa_dev, MWI_EINVAL, "null argument");
+        mwi_mesh* M = P->mesh;
+        const Topology& T = M->T;
+        ensure_p1(M);
+        const double2* k = reinterpret_cast<const double2*>(kappa_dev);
+        check_finite_device(P, k, T.nv, "kappa");
+        cudaStream_t st = P->st;
+        P->kappa.ensure(T.nv);
+        MWI_CUDA(cudaMemcpyAsync(P->kappa.p, k, T.nv * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        // beta and the interface wavenumber from the centroid value; the mass term from kappa itself
+        launch_p1_centroid(T.nt, M->tv.p, P->kappa.p, P->eps.p, st);
+        P->Mk.ensure((size_t)T.nt * M->tabs.npack);
+        launch_p1_mass(T.nt, M->tabs.npack, M->tv.p, P->kappa.p, M->Mv.p, P->Mk.p, st);
+        P->p1 = true;
+        refresh_operator(P);
     });
 }
 
-mwi_status mwi_p1_gradient(mwi_mesh_t M, const double* grad_tet_dev, const double* kappa_dev, double alpha,
-                           double* grad_vertex_dev, double* penalty, void* stream) {
-    return guard([&] {
-        MWI_REQUIRE(M && grad_tet_dev && kappa_dev && grad_vertex_dev, MWI_EINVAL, "null argument");
+mwi_status mwi_misfit_and_gradient_kappa_device(mwi_problem_t P, const double* S_meas_dev, const double* w_dev,
+                                                double alpha, double* J_out, double* R_out,
+                                                double* dPhi_dkappa_dev, mwi_solve_info* info) {
+    mwi_status status = MWI_OK;
+    mwi_status g = guard([&] {
+        MWI_REQUIRE(P && S_meas_dev && J_out && dPhi_dkappa_dev, MWI_EINVAL, "null argument");
         MWI_REQUIRE(alpha >= 0.0 && std::isfinite(alpha), MWI_EINVAL, "alpha must be finite and >= 0");
-        ensure_p1(M);
-        cudaStream_t st = (cudaStream_t)stream;
-        const int64_t nv = M->T.nv;
-        launch_p1_gradient(nv, M->v2t_ptr.p, M->v2t.p, (const double2*)grad_tet_dev, M->p1_rp.p, M->p1_col.p,
-                           M->p1_val.p, (const double2*)kappa_dev, alpha, (double2*)grad_vertex_dev,
-                           M->p1_partial.p, st);
-        if (penalty) {
-            std::lock_guard<std::mutex> lk(M->mu);
-            const size_t nb = M->p1_partial_host.size();
-            MWI_CUDA(cudaMemcpyAsync(M->p1_partial_host.data(), M->p1_partial.p, nb * sizeof(double),
-                                     cudaMemcpyDeviceToHost, st));
-            MWI_CUDA(cudaStreamSynchronize(st));
-            double sum = 0.0;
-            for (size_t b = 0; b < nb; ++b) sum += M->p1_partial_host[b];
-            *penalty = 0.5 * alpha * sum;
+        MWI_REQUIRE(P->p1, MWI_ESTATE, "no nodal parameter: call mwi_update_kappa_device first");
+        misfit_and_adjoint(P, S_meas_dev, w_dev, true, info, status);
+        mwi_mesh* M = P->mesh;
+        const Topology& T = M->T;
+        cudaStream_t st = P->st;
+        P->grad_tw.ensure((size_t)T.nt * 4);
+        launch_p1_tet_gradient(T.order, T.nt, P->m_fwd, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p,
+                               M->face_dofs.p, M->Mv.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, P->grad_tw.p,
+                               st);
+        const int nb = p1_gradient_blocks(T.nv);
+        P->p1_partial.ensure(nb);
+        P->p1_partial_host.resize(nb);
+        launch_p1_gradient(T.nv, M->v2t_ptr.p, M->v2t.p, M->tv.p, P->grad_tw.p, M->p1_rp.p, M->p1_col.p,
+                           M->p1_val.p, P->kappa.p, alpha, reinterpret_cast<double2*>(dPhi_dkappa_dev),
+                           P->p1_partial.p, st);
+        MWI_CUDA(cudaMemcpyAsync(J_out, P->J_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaMemcpyAsync(P->p1_partial_host.data(), P->p1_partial.p, nb * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+        MWI_CUDA(cudaStreamSynchronize(st));
+        double sum = 0.0;
+        for (int b = 0; b < nb; ++b) sum += P->p1_partial_host[b];
+        if (R_out) *R_out = 0.5 * alpha * sum;
+        P->have_adj = true;
+    });
+    return g != MWI_OK ? g : status;
+}
+
+mwi_status mwi_normalised_weights(const double* S_empty, int64_t count, double* w_out) {
+    return guard([&] {
+        MWI_REQUIRE(S_empty && w_out && count >= 0, MWI_EINVAL, "bad argument");
+        for (int64_t e = 0; e < count; ++e) {
+            const double a = S_empty[2 * e] * S_empty[2 * e] + S_empty[2 * e + 1] * S_empty[2 * e + 1];
+            MWI_REQUIRE(a > 0.0 && std::isfinite(a), MWI_EINVAL,
+                        "S_empty entry " + std::to_string(e) + " is zero or not finite");
+            w_out[e] = 1.0 / a;
         }
     });
 }
@@ -1407,5 +1487,7 @@ mwi_status mwi_kernel_times(mwi_problem_t P, double* ms, int64_t* counts, int32_
 }
 
 int64_t mwi_launch_count(void) { return g_launches.load(); }
+
+int64_t mwi_device_alloc_count(void) { return g_device_allocs.load(); }
 
 }  // extern "C"

@@ -68,6 +68,7 @@ void build_element_tables(int order, ElementTables& tab) {
     tab.nl = nl;
     tab.npack = nl * (nl + 1) / 2;
     tab.m_terms.clear();
+    tab.mv_c.clear();
     tab.k_terms.clear();
     tab.m_ptr.assign(1, 0);
     tab.k_ptr.assign(1, 0);
@@ -82,6 +83,12 @@ void build_element_tables(int order, ElementTables& tab) {
                     t.a = (int8_t)p.g;
                     t.b = (int8_t)q.g;
                     tab.m_terms.push_back(t);
+                    // the same term weighted by lambda_w (nodal parameter): one more power of lambda_w
+                    for (int w = 0; w < 4; ++w) {
+                        g[w]++;
+                        tab.mv_c.push_back(6.0 * p.c * q.c * moment(g, 3));
+                        g[w]--;
+                    }
                 }
             tab.m_ptr.push_back((int32_t)tab.m_terms.size());
             for (const Term& p : B[i])
@@ -195,6 +202,27 @@ __global__ void elem_geom_kernel(const double* __restrict__ xyz, const int32_t* 
     }
 }
 
+// Mv[t][w][p] = |t| sum_q mv_c[4 q + w] G[a_q][b_q]: the element mass weighted by
+// the barycentric lambda_w (local vertex w of the sorted tet)
+__global__ void elem_vertex_mass_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tv, int64_t nt,
+                                        const MTerm* __restrict__ mt, const int32_t* __restrict__ mptr,
+                                        const double* __restrict__ mv_c, int npack, double* __restrict__ Mv) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double G[4][4], vol;
+    tet_gram(xyz, tv, t, G, vol);
+    for (int p = 0; p < npack; ++p) {
+        double m[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int q = mptr[p]; q < mptr[p + 1]; ++q) {
+            const double g = G[mt[q].a][mt[q].b];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) m[w] += mv_c[4 * q + w] * g;
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) Mv[(t * 4 + w) * npack + p] = m[w] * vol;
+    }
+}
+
 __global__ void face_geom_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tv,
                                  const int32_t* __restrict__ face_tets, const int8_t* __restrict__ face_lf,
                                  int64_t nf, const FTerm* __restrict__ ft, const int32_t* __restrict__ fptr,
@@ -238,7 +266,8 @@ __global__ void slot_fill_kernel(int64_t nslots, const int64_t* __restrict__ slo
                                  const double* __restrict__ Mp, int npack, const double* __restrict__ Bf,
                                  int npack_f, const int32_t* __restrict__ fu_face,
                                  const double2* __restrict__ fu_coef, const double2* __restrict__ eps,
-                                 double k0sq, double2* __restrict__ out64, OutC* __restrict__ outlo) {
+                                 const double2* __restrict__ Mk, double k0sq, double2* __restrict__ out64,
+                                 OutC* __restrict__ outlo) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= nslots) return;
     double vr = 0.0, vi = 0.0;
@@ -253,10 +282,17 @@ __global__ void slot_fill_kernel(int64_t nslots, const int64_t* __restrict__ slo
             vi += cf.y * b;
         } else {
             int64_t t = c >> 16;
-            double k = Kp[t * npack + pair], m = Mp[t * npack + pair];
-            double2 e = eps[t];
-            vr += k - k0sq * e.x * m;
-            vi += -k0sq * e.y * m;
+            const double k = Kp[t * npack + pair];
+            if (Mk) {  // nodal parameter: the tet's own complex mass sum_w kappa_w M_t^(w)
+                const double2 mk = Mk[t * npack + pair];
+                vr += k - k0sq * mk.x;
+                vi += -k0sq * mk.y;
+            } else {
+                const double m = Mp[t * npack + pair];
+                const double2 e = eps[t];
+                vr += k - k0sq * e.x * m;
+                vi += -k0sq * e.y * m;
+            }
         }
     }
     if (out64) out64[s] = mk(vr, vi);
@@ -268,6 +304,14 @@ void launch_elem_geom(const double* xyz, const int32_t* tv, int64_t nt, const El
     int th = 128;
     elem_geom_kernel<<<(unsigned)((nt + th - 1) / th), th, 0, st>>>(
         xyz, tv, nt, tab.m_terms.p, tab.m_ptr.p, tab.k_terms.p, tab.k_ptr.p, tab.npack, K, M);
+    MWI_CHECK_LAUNCH();
+}
+
+void launch_elem_vertex_mass(const double* xyz, const int32_t* tv, int64_t nt, const ElementTablesDev& tab,
+                             double* Mv, cudaStream_t st) {
+    int th = 128;
+    elem_vertex_mass_kernel<<<(unsigned)((nt + th - 1) / th), th, 0, st>>>(xyz, tv, nt, tab.m_terms.p, tab.m_ptr.p,
+                                                                         tab.mv_c.p, tab.npack, Mv);
     MWI_CHECK_LAUNCH();
 }
 
@@ -289,11 +333,12 @@ void launch_face_coef(const int32_t* fu_tet, int64_t nfu, const double2* eps, do
 
 void launch_slot_fill(const SlotMatrixDev& S, const double* K, const double* M, int npack, const double* Bf,
                       int npack_f, const int32_t* fu_face, const double2* fu_coef, const double2* eps, double k0,
-                      double2* out64, float2* out32, cudaStream_t st) {
+                      double2* out64, float2* out32, cudaStream_t st, const double2* Mk) {
     if (S.nnz == 0) return;
     int th = 256;
     slot_fill_kernel<float2><<<(unsigned)((S.nnz + th - 1) / th), th, 0, st>>>(
-        S.nnz, S.slot_ptr.p, S.contrib.p, K, M, npack, Bf, npack_f, fu_face, fu_coef, eps, k0 * k0, out64, out32);
+        S.nnz, S.slot_ptr.p, S.contrib.p, K, M, npack, Bf, npack_f, fu_face, fu_coef, eps, Mk, k0 * k0, out64,
+        out32);
     MWI_CHECK_LAUNCH();
 }
 

@@ -25,6 +25,8 @@ void set_last_error(const std::string& msg);
 
 // kernels launched by this library (every launch site ends in MWI_CHECK_LAUNCH)
 extern std::atomic<int64_t> g_launches;
+// device allocations made by this library (every cudaMalloc goes through DevBuf)
+extern std::atomic<int64_t> g_device_allocs;
 
 #define MWI_CUDA(call)                                                                  \
     do {                                                                                \
@@ -64,6 +66,7 @@ struct DevBuf {
     void alloc(size_t count) {
         release();
         if (count == 0) return;
+        g_device_allocs.fetch_add(1, std::memory_order_relaxed);
         cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;

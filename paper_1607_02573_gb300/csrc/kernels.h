@@ -18,6 +18,7 @@ struct FTerm { double c; int8_t a, b, d, pad[5]; };
 struct ElementTables {
     int nl = 0, npack = 0, nlf = 0, npack_f = 0;
     std::vector<MTerm> m_terms;
+    std::vector<double> mv_c;     // per m_term, 4 coefficients of the lambda_w-weighted mass (w = 0..3)
     std::vector<int32_t> m_ptr;
     std::vector<KTerm> k_terms;
     std::vector<int32_t> k_ptr;
@@ -28,6 +29,7 @@ struct ElementTables {
 struct ElementTablesDev {
     int nl = 0, npack = 0, nlf = 0, npack_f = 0;
     DevBuf<MTerm> m_terms;
+    DevBuf<double> mv_c;
     DevBuf<int32_t> m_ptr;
     DevBuf<KTerm> k_terms;
     DevBuf<int32_t> k_ptr;
@@ -51,9 +53,14 @@ void launch_face_geom(const double* xyz, const int32_t* tv, const int32_t* face_
                       int64_t nf, const ElementTablesDev& tab, double* Bf, cudaStream_t st);
 void launch_face_coef(const int32_t* fu_tet, int64_t nfu, const double2* eps, double k0, double2* coef,
                       cudaStream_t st);
+// Mk (nullable): per-tet complex mass sum_w kappa_w M_t^(w) [nt][npack] of a nodal
+// parameter, used in place of eps_t M_t
 void launch_slot_fill(const SlotMatrixDev& S, const double* K, const double* M, int npack, const double* Bf,
                       int npack_f, const int32_t* fu_face, const double2* fu_coef, const double2* eps, double k0,
-                      double2* out64, float2* out32, cudaStream_t st);
+                      double2* out64, float2* out32, cudaStream_t st, const double2* Mk = nullptr);
+// vertex-weighted element masses Mv[t][w][pair] = int_t lambda_w N_i . N_j
+void launch_elem_vertex_mass(const double* xyz, const int32_t* tv, int64_t nt, const ElementTablesDev& tab,
+                             double* Mv, cudaStream_t st);
 
 // ---- multifrontal factorisation and ORAS application (factor.cu, sweep.cu, oras.cu)
 // One GEMM tile of the sweeps: the front's geometry and the tile's first row.
@@ -152,11 +159,23 @@ void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const do
 struct Topology;
 void build_p1_stiffness(const Topology& T, std::vector<int32_t>& rp, std::vector<int32_t>& col,
                         std::vector<double>& val);
-void launch_p1_tet_eps(int64_t nt, const int32_t* tv, const double2* kappa, double2* eps, cudaStream_t st);
+// eps_t = kappa at the tet's centroid; Mk[t][p] = sum_w kappa_{v_w(t)} Mv[t][w][p]
+void launch_p1_centroid(int64_t nt, const int32_t* tv, const double2* kappa, double2* eps, cudaStream_t st);
+void launch_p1_mass(int64_t nt, int npack, const int32_t* tv, const double2* kappa, const double* Mv, double2* Mk,
+                    cudaStream_t st);
+// per (tet, local vertex): conj of k0^2 sum_j lam^T M_t^(w) u + 1/4 of the tet's beta term
+void launch_p1_tet_gradient(int order, int64_t nt, int m, const int32_t* tet_dofs, const int32_t* tet_faces,
+                            const int8_t* face_tag, const int32_t* face_dofs, const double* Mv, const double* Bf,
+                            const double2* eps, double k0, const double2* U, const double2* Lam, double2* out_tw,
+                            cudaStream_t st);
 int p1_gradient_blocks(int64_t nv);
-void launch_p1_gradient(int64_t nv, const int32_t* v2t_ptr, const int32_t* v2t, const double2* grad_t,
-                        const int32_t* rp, const int32_t* col, const double* val, const double2* kappa, double alpha,
-                        double2* out, double* partial, cudaStream_t st);
+// per vertex: the (tet, vertex) gradients of its tets plus alpha K kappa;
+// partial[block] = the block's sum of Re(conj(kappa_v) (K kappa)_v)
+void launch_p1_gradient(int64_t nv, const int32_t* v2t_ptr, const int32_t* v2t, const int32_t* tv,
+                        const double2* grad_tw, const int32_t* rp, const int32_t* col, const double* val,
+                        const double2* kappa, double alpha, double2* out, double* partial, cudaStream_t st);
+// number of entries of a complex array with a non-finite part, into *count (device)
+void launch_count_nonfinite(int64_t n, const double2* x, int* count, cudaStream_t st);
 
 // ---- Krylov building blocks (krylov.cu)
 template <typename C>

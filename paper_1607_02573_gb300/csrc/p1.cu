@@ -1,10 +1,18 @@
-// Nodal (P1) permittivity parameter with a gradient penalty (the P1 parameter
-// of Section 6.3 and the regularised, normalised misfit of Eq. defJ2):
-//   eps_t = (kappa at the tet's centroid) = 1/4 sum of kappa at its vertices
-//   R     = (alpha / 2) Re(kappa^H K kappa),  K the P1 stiffness matrix
-//   dPhi/dRe kappa_v + i dPhi/dIm kappa_v = 1/4 sum_{t contains v} g_t + alpha (K kappa)_v
-// with g_t the per-tet gradient (same convention) of the misfit.  The spreading
-// sums each vertex's tets in ascending order, so it is deterministic.
+// Nodal (P1) permittivity parameter with a gradient penalty (the piecewise
+// linear parameter of Section 6.3 and the regularised, normalised misfit of
+// Eq. defJ2).  kappa(x) = sum_v kappa_v lambda_v(x) varies inside every tet:
+//   mass term  int_t kappa N_i . N_j = sum_w kappa_{v_w(t)} M_t^(w)[i, j],
+//              M_t^(w) = int_t lambda_w N_i . N_j   (vertex-weighted masses)
+//   beta on impedance faces and the interface wavenumber of the local
+//   problems use the P1 field at the owning tet's centroid,
+//              kappa_bar_t = 1/4 sum_w kappa_{v_w(t)}
+//   gradient   G_v = sum over the (tet, local vertex) pairs of v of
+//              k0^2 sum_j lam_{j,t}^T M_t^(w) u_{j,t}
+//              + 1/4 sum_j lam_{j,t}^T (-i k0 / (2 sqrt(kappa_bar_t))) B_t u_{j,t}
+//   penalty    R = (alpha / 2) Re(kappa^H K kappa),  K the P1 stiffness matrix
+//   returned   dPhi/dRe kappa_v + i dPhi/dIm kappa_v = conj(G_v) + alpha (K kappa)_v.
+// Every sum runs in a fixed order (a vertex's tets ascending), so the results
+// are deterministic.
 #include <algorithm>
 
 #include "common.h"
@@ -13,8 +21,8 @@
 
 namespace mwi {
 
-__global__ void p1_tet_eps_kernel(int64_t nt, const int32_t* __restrict__ tv, const double2* __restrict__ kappa,
-                                  double2* __restrict__ eps) {
+__global__ void p1_centroid_kernel(int64_t nt, const int32_t* __restrict__ tv, const double2* __restrict__ kappa,
+                                   double2* __restrict__ eps) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
     const int32_t* v = tv + 4 * t;
@@ -28,11 +36,139 @@ __global__ void p1_tet_eps_kernel(int64_t nt, const int32_t* __restrict__ tv, co
     eps[t] = make_double2(0.25 * s.x, 0.25 * s.y);
 }
 
-// per vertex: the spread per-tet gradient plus alpha K kappa; per block, the
-// fixed-order sum of Re(conj(kappa_v) (K kappa)_v) over its vertices
+// Mk[t][p] = sum_w kappa_{v_w(t)} Mv[t][w][p], one thread per (tet, pair)
+__global__ void p1_mass_kernel(int64_t nt, int npack, const int32_t* __restrict__ tv,
+                               const double2* __restrict__ kappa, const double* __restrict__ Mv,
+                               double2* __restrict__ Mk) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nt * npack) return;
+    const int64_t t = e / npack;
+    const int p = (int)(e - t * npack);
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const double2 k = kappa[tv[4 * t + w]];
+        const double m = Mv[(t * 4 + w) * npack + p];
+        acc.x += k.x * m;
+        acc.y += k.y * m;
+    }
+    Mk[e] = acc;
+}
+
+// one warp per tet: the four (tet, vertex) gradient terms, reduced over the
+// m columns (lanes take columns, fixed shuffle order)
+template <int NL, int NLF>
+__global__ void __launch_bounds__(256) p1_tet_gradient_kernel(
+    int64_t nt, int m, const int32_t* __restrict__ tet_dofs, const int32_t* __restrict__ tet_faces,
+    const int8_t* __restrict__ face_tag, const int32_t* __restrict__ face_dofs, const double* __restrict__ Mv,
+    const double* __restrict__ Bf, const double2* __restrict__ eps, double k0, const double2* __restrict__ U,
+    const double2* __restrict__ Lam, double2* __restrict__ out) {
+    constexpr int NP = NL * (NL + 1) / 2;
+    constexpr int NPF = NLF * (NLF + 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nt) return;
+    int dofs[NL];
+#pragma unroll
+    for (int a = 0; a < NL; ++a) dofs[a] = tet_dofs[t * NL + a];
+    const double* M = Mv + t * 4 * NP;
+    int ff[4], nff = 0;
+#pragma unroll
+    for (int lf = 0; lf < 4; ++lf) {
+        const int f = tet_faces[t * 4 + lf];
+        if (face_tag[f] == 2) ff[nff++] = f;
+    }
+    double vr[4] = {0.0, 0.0, 0.0, 0.0}, vi[4] = {0.0, 0.0, 0.0, 0.0};
+    double br = 0.0, bi = 0.0;
+    for (int c = lane; c < m; c += 32) {
+        double2 u[NL], l[NL];
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+            if (dofs[a] >= 0) {
+                u[a] = U[(int64_t)dofs[a] * m + c];
+                l[a] = Lam[(int64_t)dofs[a] * m + c];
+            } else {
+                u[a] = make_double2(0.0, 0.0);
+                l[a] = make_double2(0.0, 0.0);
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+#pragma unroll
+            for (int a = 0; a < NL; ++a) {
+                double2 mu = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int b = 0; b < NL; ++b) {
+                    const int ia = a < b ? a : b, ib = a < b ? b : a;
+                    const double mab = M[w * NP + ia * NL - ia * (ia - 1) / 2 + (ib - ia)];
+                    mu.x += mab * u[b].x;
+                    mu.y += mab * u[b].y;
+                }
+                vr[w] += l[a].x * mu.x - l[a].y * mu.y;
+                vi[w] += l[a].x * mu.y + l[a].y * mu.x;
+            }
+        }
+        for (int q = 0; q < nff; ++q) {
+            const int f = ff[q];
+            double2 uf[NLF], lf_[NLF];
+#pragma unroll
+            for (int a = 0; a < NLF; ++a) {
+                const int d = face_dofs[(int64_t)f * NLF + a];
+                uf[a] = d >= 0 ? U[(int64_t)d * m + c] : make_double2(0.0, 0.0);
+                lf_[a] = d >= 0 ? Lam[(int64_t)d * m + c] : make_double2(0.0, 0.0);
+            }
+            const double* Bp = Bf + (int64_t)f * NPF;
+#pragma unroll
+            for (int a = 0; a < NLF; ++a) {
+                double2 bu = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int b = 0; b < NLF; ++b) {
+                    const int ia = a < b ? a : b, ib = a < b ? b : a;
+                    const double bab = Bp[ia * NLF - ia * (ia - 1) / 2 + (ib - ia)];
+                    bu.x += bab * uf[b].x;
+                    bu.y += bab * uf[b].y;
+                }
+                br += lf_[a].x * bu.x - lf_[a].y * bu.y;
+                bi += lf_[a].x * bu.y + lf_[a].y * bu.x;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            vr[w] += __shfl_xor_sync(0xffffffffu, vr[w], o);
+            vi[w] += __shfl_xor_sync(0xffffffffu, vi[w], o);
+        }
+        br += __shfl_xor_sync(0xffffffffu, br, o);
+        bi += __shfl_xor_sync(0xffffffffu, bi, o);
+    }
+    if (lane == 0) {
+        // 1/4 of the beta term: coef = -i k0 / (2 sqrt(kappa_bar_t))
+        double qr = 0.0, qi = 0.0;
+        if (nff > 0) {
+            const double2 e = eps[t];
+            const double r = sqrt(e.x * e.x + e.y * e.y);
+            double sx = sqrt(0.5 * (r + e.x)), sy = sqrt(0.5 * (r - e.x));
+            if (e.y < 0) sy = -sy;
+            const double den = 2.0 * (sx * sx + sy * sy);
+            const double cr = -k0 * sy / den;
+            const double ci = -k0 * sx / den;
+            qr = 0.25 * (cr * br - ci * bi);
+            qi = 0.25 * (cr * bi + ci * br);
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            out[4 * t + w] = make_double2(k0 * k0 * vr[w] + qr, -(k0 * k0 * vi[w] + qi));
+    }
+}
+
+// per vertex: the (tet, vertex) gradients of its tets in ascending tet order plus
+// alpha K kappa; per block, the fixed-order sum of Re(conj(kappa_v) (K kappa)_v)
 __global__ void __launch_bounds__(256) p1_gradient_kernel(int64_t nv, const int32_t* __restrict__ v2t_ptr,
                                                           const int32_t* __restrict__ v2t,
-                                                          const double2* __restrict__ grad_t,
+                                                          const int32_t* __restrict__ tv,
+                                                          const double2* __restrict__ grad_tw,
                                                           const int32_t* __restrict__ rp,
                                                           const int32_t* __restrict__ col,
                                                           const double* __restrict__ val,
@@ -44,7 +180,10 @@ __global__ void __launch_bounds__(256) p1_gradient_kernel(int64_t nv, const int3
     if (v < nv) {
         double2 g = make_double2(0.0, 0.0);
         for (int32_t q = v2t_ptr[v]; q < v2t_ptr[v + 1]; ++q) {
-            const double2 x = grad_t[v2t[q]];
+            const int64_t t = v2t[q];
+            int w = 0;
+            while (w < 3 && tv[4 * t + w] != (int32_t)v) ++w;
+            const double2 x = grad_tw[4 * t + w];
             g.x += x.x;
             g.y += x.y;
         }
@@ -54,7 +193,7 @@ __global__ void __launch_bounds__(256) p1_gradient_kernel(int64_t nv, const int3
             kk.x += val[q] * x.x;
             kk.y += val[q] * x.y;
         }
-        out[v] = make_double2(0.25 * g.x + alpha * kk.x, 0.25 * g.y + alpha * kk.y);
+        out[v] = make_double2(g.x + alpha * kk.x, g.y + alpha * kk.y);
         const double2 kv = kappa[v];
         e = kv.x * kk.x + kv.y * kk.y;
     }
@@ -65,6 +204,17 @@ __global__ void __launch_bounds__(256) p1_gradient_kernel(int64_t nv, const int3
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// counts entries with a non-finite real or imaginary part
+__global__ void count_nonfinite_kernel(int64_t n, const double2* __restrict__ x, int* __restrict__ count) {
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = x[i];
+        bad += (isfinite(v.x) && isfinite(v.y)) ? 0 : 1;
+    }
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(count, bad);
 }
 
 void build_p1_stiffness(const Topology& T, std::vector<int32_t>& rp, std::vector<int32_t>& col,
@@ -128,18 +278,47 @@ void build_p1_stiffness(const Topology& T, std::vector<int32_t>& rp, std::vector
     }
 }
 
-void launch_p1_tet_eps(int64_t nt, const int32_t* tv, const double2* kappa, double2* eps, cudaStream_t st) {
-    p1_tet_eps_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, tv, kappa, eps);
+void launch_p1_centroid(int64_t nt, const int32_t* tv, const double2* kappa, double2* eps, cudaStream_t st) {
+    p1_centroid_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, tv, kappa, eps);
+    MWI_CHECK_LAUNCH();
+}
+
+void launch_p1_mass(int64_t nt, int npack, const int32_t* tv, const double2* kappa, const double* Mv, double2* Mk,
+                    cudaStream_t st) {
+    const int64_t n = nt * npack;
+    p1_mass_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nt, npack, tv, kappa, Mv, Mk);
+    MWI_CHECK_LAUNCH();
+}
+
+void launch_p1_tet_gradient(int order, int64_t nt, int m, const int32_t* tet_dofs, const int32_t* tet_faces,
+                            const int8_t* face_tag, const int32_t* face_dofs, const double* Mv, const double* Bf,
+                            const double2* eps, double k0, const double2* U, const double2* Lam, double2* out_tw,
+                            cudaStream_t st) {
+    const int th = 256;
+    const unsigned blocks = (unsigned)((nt * 32 + th - 1) / th);
+    if (order == 1)
+        p1_tet_gradient_kernel<6, 3><<<blocks, th, 0, st>>>(nt, m, tet_dofs, tet_faces, face_tag, face_dofs, Mv, Bf,
+                                                            eps, k0, U, Lam, out_tw);
+    else
+        p1_tet_gradient_kernel<20, 8><<<blocks, th, 0, st>>>(nt, m, tet_dofs, tet_faces, face_tag, face_dofs, Mv,
+                                                             Bf, eps, k0, U, Lam, out_tw);
     MWI_CHECK_LAUNCH();
 }
 
 int p1_gradient_blocks(int64_t nv) { return (int)((nv + 255) / 256); }
 
-void launch_p1_gradient(int64_t nv, const int32_t* v2t_ptr, const int32_t* v2t, const double2* grad_t,
-                        const int32_t* rp, const int32_t* col, const double* val, const double2* kappa, double alpha,
-                        double2* out, double* partial, cudaStream_t st) {
-    p1_gradient_kernel<<<p1_gradient_blocks(nv), 256, 0, st>>>(nv, v2t_ptr, v2t, grad_t, rp, col, val, kappa, alpha,
-                                                               out, partial);
+void launch_p1_gradient(int64_t nv, const int32_t* v2t_ptr, const int32_t* v2t, const int32_t* tv,
+                        const double2* grad_tw, const int32_t* rp, const int32_t* col, const double* val,
+                        const double2* kappa, double alpha, double2* out, double* partial, cudaStream_t st) {
+    p1_gradient_kernel<<<p1_gradient_blocks(nv), 256, 0, st>>>(nv, v2t_ptr, v2t, tv, grad_tw, rp, col, val, kappa,
+                                                               alpha, out, partial);
+    MWI_CHECK_LAUNCH();
+}
+
+void launch_count_nonfinite(int64_t n, const double2* x, int* count, cudaStream_t st) {
+    if (n <= 0) return;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    count_nonfinite_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, x, count);
     MWI_CHECK_LAUNCH();
 }
 

@@ -79,12 +79,13 @@ _SIGS = {
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
     "mwi_problem_device_bytes": [_vp, _i64p],
     "mwi_oras_traffic": [_vp, C.c_int32, _dp],
-    "mwi_p1_tet_eps": [_vp, _vp, _vp, _vp],
-    "mwi_p1_gradient": [_vp, _vp, _vp, C.c_double, _vp, _dp, _vp],
+    "mwi_update_kappa_device": [_vp, _vp],
+    "mwi_misfit_and_gradient_kappa_device": [_vp, _vp, _vp, C.c_double, _dp, _dp, _vp, C.POINTER(mwi_solve_info)],
+    "mwi_normalised_weights": [_dp, C.c_int64, _dp],
     "mwi_kernel_times": [_vp, _dp, _i64p, C.c_int32],
     "mwi_misfit": [_vp, _dp, _dp, _dp],
 }
-EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count"])
+EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -97,12 +98,23 @@ mwi_last_error = _lib.mwi_last_error
 _lib.mwi_launch_count.argtypes = []
 _lib.mwi_launch_count.restype = C.c_int64
 mwi_launch_count = _lib.mwi_launch_count
+_lib.mwi_device_alloc_count.argtypes = []
+_lib.mwi_device_alloc_count.restype = C.c_int64
+mwi_device_alloc_count = _lib.mwi_device_alloc_count
 
 
 def check(status, allow=()):
     if status != MWI_OK and status not in allow:
         raise MwiError(status, (mwi_last_error() or b"").decode())
     return status
+
+
+def normalised_weights(S_empty):
+    """w_ij = 1 / |S_empty_ij|^2 (Eq. defJ2), computed by the library."""
+    S = np.ascontiguousarray(S_empty, dtype=np.complex128)
+    w = np.empty(S.shape, dtype=np.float64)
+    check(mwi_normalised_weights(_ptr(S.view(np.float64), C.c_double), S.size, _ptr(w, C.c_double)))
+    return w
 
 
 def _ptr(a, ctype):
@@ -143,6 +155,7 @@ class Mesh:
         self.tet = np.ascontiguousarray(tet, dtype=np.int32)
         tag = np.ascontiguousarray(bface_tag, dtype=np.int32)
         self.nt = self.tet.shape[0]
+        self.nv = self.xyz.shape[0]
         self.order = order
         h = _vp()
         check(mwi_mesh_create(_ptr(self.xyz, C.c_double), self.xyz.shape[0], _ptr(self.tet, C.c_int32), self.nt,
@@ -151,29 +164,6 @@ class Mesh:
         n = C.c_int64()
         check(mwi_mesh_ndof(h, C.byref(n)))
         self.ndof = n.value
-
-    def p1_tet_eps(self, kappa, stream=None):
-        """Per-tet permittivity (device tensor [nt]) from per-vertex values kappa (device tensor [nv])."""
-        import torch
-        if stream is None:
-            stream = torch.cuda.current_stream()
-        k = kappa.to(torch.complex128).contiguous()
-        eps = torch.empty(self.nt, dtype=torch.complex128, device=k.device)
-        check(mwi_p1_tet_eps(self.h, _vp(k.data_ptr()), _vp(eps.data_ptr()), _vp(stream.cuda_stream)))
-        return eps
-
-    def p1_gradient(self, grad_tet, kappa, alpha, stream=None):
-        """Per-vertex gradient (device tensor [nv]) of J(eps(kappa)) + R(kappa) and the penalty R."""
-        import torch
-        if stream is None:
-            stream = torch.cuda.current_stream()
-        g = grad_tet.to(torch.complex128).contiguous()
-        k = kappa.to(torch.complex128).contiguous()
-        out = torch.empty_like(k)
-        R = C.c_double()
-        check(mwi_p1_gradient(self.h, _vp(g.data_ptr()), _vp(k.data_ptr()), float(alpha), _vp(out.data_ptr()),
-                              C.byref(R), _vp(stream.cuda_stream)))
-        return out, R.value
 
     def dof_keys(self):
         kind = np.empty(self.ndof, dtype=np.int32)
@@ -274,6 +264,31 @@ class Problem:
         check(st, allow=(MWI_ENOTCONV,) if allow_notconv else ())
         self.info = info
         return J.value, grad
+
+    def update_kappa(self, kappa):
+        """Reassemble (and refactor) for the nodal parameter kappa (device tensor [nv])."""
+        import torch
+        k = kappa.to(torch.complex128).contiguous()
+        check(mwi_update_kappa_device(self.h, _vp(k.data_ptr())))
+
+    def misfit_and_gradient_kappa(self, S_meas, w=None, alpha=0.0, allow_notconv=False):
+        """J, R and the per-vertex gradient of J + R (device tensor [nv]) for the
+        nodal parameter of the last update_kappa; S_meas, w host arrays [n_rx, n_tx]."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Sm = torch.from_numpy(np.ascontiguousarray(np.asarray(S_meas, dtype=np.complex128).T)).to(dev)
+        wd = None
+        if w is not None:
+            wd = torch.from_numpy(np.ascontiguousarray(np.asarray(w, dtype=np.float64).T)).to(dev)
+        grad = torch.empty(self.mesh.nv, dtype=torch.complex128, device=dev)
+        J, R = C.c_double(), C.c_double()
+        info = mwi_solve_info()
+        st = mwi_misfit_and_gradient_kappa_device(self.h, _vp(Sm.data_ptr()),
+                                                  _vp(wd.data_ptr()) if wd is not None else None, float(alpha),
+                                                  C.byref(J), C.byref(R), _vp(grad.data_ptr()), C.byref(info))
+        check(st, allow=(MWI_ENOTCONV,) if allow_notconv else ())
+        self.info = info
+        return J.value, R.value, grad
 
     def fields(self, which=0):
         """Borrowed device pointer and shape (n, m) of the resident fields."""

@@ -66,3 +66,28 @@ def test_struct_layouts_match_the_header(tmp_path):
         st = structs[name]
         want = ctypes.sizeof(st) if what == "size" else getattr(st, what).offset
         assert int(val) == want, (name, what, int(val), want)
+
+
+def test_mesh_create_rejects_bad_meshes_on_the_host():
+    """Mesh validation happens on the host before any device work: a degenerate
+    or vertex-repeating tet, an out-of-range vertex id and a bad boundary tag
+    each give MWI_EINVAL with a message (no GPU needed)."""
+    import numpy as np
+
+    from paper_1607_02573_gb300 import mwi
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0]], dtype=np.float64)
+    good = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    tag = np.zeros((1, 4), dtype=np.int32)
+    cases = {
+        "degenerate": (np.array([[0, 1, 2, 4]], dtype=np.int32), tag),  # four coplanar vertices
+        "repeat": (np.array([[0, 1, 1, 3]], dtype=np.int32), tag),
+        "range": (np.array([[0, 1, 2, 7]], dtype=np.int32), tag),
+        "tag": (good, np.array([[0, 3, 0, 0]], dtype=np.int32)),
+    }
+    for name, (tet, tg) in cases.items():
+        h = ctypes.c_void_p()
+        st = mwi.mwi_mesh_create(mwi._ptr(xyz, ctypes.c_double), xyz.shape[0], mwi._ptr(tet, ctypes.c_int32), 1,
+                                 mwi._ptr(tg, ctypes.c_int32), 1, ctypes.byref(h))
+        assert st == mwi.MWI_EINVAL, name
+        assert mwi.mwi_last_error(), name
+        assert not h.value, name

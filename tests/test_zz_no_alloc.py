@@ -6,8 +6,11 @@ a latency-critical loop that must not pay cudaMalloc's implicit device
 synchronisation).  It takes its scratch from a fixed 32 MiB device array
 instead of allocating.  Here it must give the same result as
 mwi_oras_apply_device, through the C ABI, on two calls in a row (the shared
-scratch keeps the previous call's contents), in the FP64 and the mixed path,
-and it must reject a problem whose scratch would not fit.
+scratch keeps the previous call's contents), in the FP64 and the mixed path:
+bit for bit, since both run the same kernels on the same inputs.  Once the
+first call has looked up the scratch array's address, a call makes no device
+allocation (the library's cudaMalloc counter does not move).  A problem whose
+scratch would not fit is rejected.
 
 This file is collected last so that a failure here stops a -x run only after
 every other test has run.
@@ -51,13 +54,18 @@ def test_noalloc_matches_regular_entry_point(lib, precision):
         y_ref = torch.empty_like(x)
         y_new = torch.full_like(x, float("nan"))
         lib.check(lib.mwi_oras_apply_device(P.h, C.c_void_p(x.data_ptr()), C.c_void_p(y_ref.data_ptr()), m))
+        torch.cuda.synchronize()
+        n_alloc = lib.mwi_device_alloc_count()
         lib.check(lib.mwi_oras_apply_device_noalloc(P.h, C.c_void_p(x.data_ptr()), C.c_void_p(y_new.data_ptr()),
                                                     m))
         torch.cuda.synchronize()
+        if call > 0:
+            assert lib.mwi_device_alloc_count() == n_alloc, f"call {call}: the library allocated device memory"
         a = y_new.cpu().numpy()
         b = y_ref.cpu().numpy()
         assert np.all(np.isfinite(a)), f"call {call}: non-finite output"
         assert rel_err(a, b) <= TOL[precision], f"call {call}"
+        assert np.array_equal(a, b), f"call {call}: not bit for bit"
     P.close()
     M.close()
 
