@@ -114,6 +114,8 @@ struct mwi_problem {
     DevBuf<float2> Aval32;
     DevBuf<double2> ws64, inv64, sch64[2];
     DevBuf<float2> ws32, inv32, sch32[2];
+    DevBuf<float> wt;        // tiled, swizzled copy of the c64 panels (tensor-core sweeps)
+    DevBuf<int> sweep_err;   // error code of the tensor-core sweeps' bounded waits
     DevBuf<int> perturbed;
     int n_perturbed = 0;
     // solve state
@@ -173,7 +175,8 @@ struct mwi_problem {
                    Bc.bytes() + Xc.bytes() + v32.bytes() + x32.bytes() + r32.bytes() + dscratch.bytes() +
                    rx_dof_d.bytes() + tx_dof_d.bytes() + rx_sign_d.bytes() + tx_sign_d.bytes() + cur_d.bytes() +
                    S_d.bytes() + Smeas_d.bytes() + r_d.bytes() + grad_d.bytes() + w_d.bytes() + J_d.bytes() +
-                   kappa.bytes() + Mk.bytes() + grad_tw.bytes() + p1_partial.bytes() + nonfinite.bytes();
+                   kappa.bytes() + Mk.bytes() + grad_tw.bytes() + p1_partial.bytes() + nonfinite.bytes() +
+                   wt.bytes() + sweep_err.bytes();
         for (int k = 0; k < 2; ++k) b += sch64[k].bytes() + sch32[k].bytes();
         return b;
     }
@@ -240,6 +243,28 @@ cudaEvent_t take_event(mwi_problem* P) {
 
 // complex FP32 sweep engine: 0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores TF32
 int tc_of(const mwi_solver_opts& o) { return o.sweep_engine == 3 ? 0 : o.sweep_engine; }
+
+// the complex FP32 sweeps of this problem: engine, tiled panels and error flag
+// of the tensor-core engine
+SweepCfg sweep_cfg(const mwi_problem* P) {
+    SweepCfg c;
+    c.tc = tc_of(P->opts);
+    c.wt = P->wt.p;
+    c.err = P->sweep_err.p;
+    return c;
+}
+
+// a tensor-core sweep whose bounded wait expired reports it here (read after a solve)
+void check_sweep_error(mwi_problem* P) {
+    if (tc_of(P->opts) != 4 || !P->sweep_err.p) return;
+    int code = 0;
+    MWI_CUDA(cudaMemcpyAsync(&code, P->sweep_err.p, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+    MWI_CUDA(cudaStreamSynchronize(P->st));
+    if (code) {
+        MWI_CUDA(cudaMemsetAsync(P->sweep_err.p, 0, sizeof(int), P->st));
+        throw Error(MWI_ETIMEOUT, "tensor-core sweep: a bounded wait expired (role " + std::to_string(code) + ")");
+    }
+}
 
 // timed region helper: records an event pair around fn when enabled
 template <typename Fn>
@@ -471,6 +496,59 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
         TL.f_tiles.upload(ft, st);
     }
     {
+        // tensor-core sweeps: tiled panel offsets, packing blocks, 128-row tiles
+        std::vector<int64_t> toff(nf);
+        std::vector<int2> pb;
+        int64_t acc = 0;
+        for (size_t k = 0; k < nf; ++k) {
+            const Front& fr = D.fronts[k];
+            toff[k] = acc;
+            acc += tiled_panel_floats(fr.p, fr.p + fr.u);
+            for (int rb = 0; rb < (fr.p + fr.u + 31) / 32; ++rb) pb.push_back(make_int2((int)k, rb));
+        }
+        F.tiled_floats = std::max<int64_t>(acc, 512);
+        F.n_pack_blocks = (int64_t)pb.size();
+        if (pb.empty()) pb.push_back(make_int2(0, 0));
+        up(F.t_off, toff, st);
+        up(F.pack_blocks, pb, st);
+        TileLists& TL = F.tiles128;
+        TL.tm = 128;
+        std::vector<TileDesc> pt, ft;
+        TL.p_ptr.assign(1, 0);
+        TL.f_ptr.assign(1, 0);
+        for (int l = 0; l < nlev; ++l) {
+            for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
+                const int sid = D.level_fronts[q];
+                const Front& fr = D.fronts[sid];
+                TileDesc d;
+                d.a_off = toff[sid];
+                d.sbase = D.sub_off[fr.sub];
+                d.rowbase = d.sbase + fr.start;
+                d.upd_row = fr.upd_row;
+                d.asm_base = D.asm_base[sid];
+                d.u_off = fr.u_off;
+                d.p = fr.p;
+                d.f = fr.p + fr.u;
+                d.pad = 0;
+                for (int r = 0; r < fr.p; r += 128) { d.row0 = r; pt.push_back(d); }
+                for (int r = 0; r < fr.p + fr.u; r += 128) { d.row0 = r; ft.push_back(d); }
+            }
+            // heaviest first (stages per tile): backward by row blocks, forward by pivot atoms
+            std::stable_sort(pt.begin() + TL.p_ptr.back(), pt.end(), [](const TileDesc& a, const TileDesc& b) {
+                return (a.f + 31) / 32 - a.row0 / 32 > (b.f + 31) / 32 - b.row0 / 32;
+            });
+            std::stable_sort(ft.begin() + TL.f_ptr.back(), ft.end(), [](const TileDesc& a, const TileDesc& b) {
+                return std::min(a.p, a.row0 + 128) > std::min(b.p, b.row0 + 128);
+            });
+            TL.p_ptr.push_back((int64_t)pt.size());
+            TL.f_ptr.push_back((int64_t)ft.size());
+        }
+        if (pt.empty()) pt.push_back(TileDesc{});
+        if (ft.empty()) ft.push_back(TileDesc{});
+        TL.p_tiles.upload(pt, st);
+        TL.f_tiles.upload(ft, st);
+    }
+    {
         std::vector<int64_t> io(D.level_fronts.size());
         F.inv_entries = 0;
         for (int l = 0; l < nlev; ++l) {
@@ -534,7 +612,16 @@ void numeric_setup(mwi_problem* P, bool refactor = true) {
         });
         timed(P, 3, [&] {
             factorize_fronts<float2>(E.F, E.ut[0], P->Bval.p, P->ws32.p, sch, P->inv32.p, P->perturbed.p, st);
+            if (tc_of(P->opts) == 4) {
+                P->wt.ensure((size_t)E.F.tiled_floats);
+                pack_tiled(E.F.pack_blocks.p, E.F.n_pack_blocks, E.F.f_off.p, E.F.t_off.p, E.F.p.p, E.F.u.p,
+                           P->ws32.p, P->wt.p, st);
+            }
         });
+        if (tc_of(P->opts) == 4 && !P->sweep_err.p) {
+            P->sweep_err.alloc(1);
+            MWI_CUDA(cudaMemsetAsync(P->sweep_err.p, 0, sizeof(int), st));
+        }
     } else {
         P->ws64.ensure(E.F.ws_total());
         P->inv64.ensure(std::max<int64_t>(1, E.F.inv_entries));
@@ -561,7 +648,7 @@ void create_problem(mwi_mesh* M, const double* eps, bool eps_dev, double freq, c
     std::unique_ptr<mwi_problem> P(new mwi_problem());
     P->opts = defaults(opts);
     MWI_REQUIRE(P->opts.precision >= 0 && P->opts.precision <= 2, MWI_EINVAL, "precision must be 0, 1 or 2");
-    MWI_REQUIRE(P->opts.sweep_engine >= 1 && P->opts.sweep_engine <= 3, MWI_EINVAL, "sweep_engine must be 0..3");
+    MWI_REQUIRE(P->opts.sweep_engine >= 1 && P->opts.sweep_engine <= 4, MWI_EINVAL, "sweep_engine must be 0..4");
     MWI_REQUIRE(P->opts.n_sub <= M->T.nt, MWI_EINVAL, "more subdomains than tets");
     P->mesh = M;
     P->st = (cudaStream_t)stream;
@@ -839,7 +926,7 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     auto M32 = [&](const float2* x, float2* y) {
         timed(P, 1, [&] {
             oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, x, y,
-                               tc_of(P->opts));
+                               sweep_cfg(P));
         });
     };
     auto M64 = [&](const double2* x, double2* y) {
@@ -957,7 +1044,7 @@ void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_sol
     auto Mop = [&](const float2* v, float2* z) {
         timed(P, 1, [&] {
             oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, v, z,
-                               tc_of(P->opts));
+                               sweep_cfg(P));
         });
     };
     G.timer = [P](int slot, const std::function<void()>& fn) { timed(P, slot, fn); };
@@ -1134,6 +1221,7 @@ mwi_status mwi_forward_solve(mwi_problem_t P, const mwi_antenna* tx, int32_t n_t
             status = MWI_ENOTCONV;
             set_last_error(e.what());
         }
+        check_sweep_error(P);
         P->S_d.ensure((size_t)n_rx * m);
         launch_s_extract(n_rx, m, P->rx_dof_d.p, P->rx_sign_d.p, P->U.p, P->S_d.p, st);
         MWI_CUDA(cudaMemcpyAsync(S_out, P->S_d.p, (size_t)n_rx * m * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -1186,6 +1274,7 @@ static void misfit_and_adjoint(mwi_problem_t P, const double* S_meas, const doub
         status = MWI_ENOTCONV;
         set_last_error(e.what());
     }
+    check_sweep_error(P);
 }
 
 static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const double* w, double* J_out,
@@ -1302,7 +1391,7 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
             P->x32.ensure(n * m);
             convert_c128_to_c64(n * m, (const double2*)x_dev, P->v32.p, P->st);
             oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, P->st, P->v32.p,
-                               P->x32.p, tc_of(P->opts));
+                               P->x32.p, sweep_cfg(P));
             convert_c64_to_c128(n * m, P->x32.p, (double2*)y_dev, P->st);
         } else {
             P->Y64.ensure((size_t)E.F.nloc * m);
@@ -1312,6 +1401,7 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
                                 P->upd64.p, P->st);
         }
         MWI_CUDA(cudaStreamSynchronize(P->st));
+        check_sweep_error(P);
     });
 }
 
@@ -1322,8 +1412,9 @@ mwi_status mwi_oras_apply_device_noalloc(mwi_problem_t P, const double* x_dev, d
         const bool mixed = P->opts.precision != 0;
         const void* ws = mixed ? (const void*)P->ws32.p : (const void*)P->ws64.p;
         oras_apply_noalloc(E.F, ws, mixed, (const double2*)x_dev, (double2*)y_dev, m, P->mesh->T.ndof, P->st,
-                           tc_of(P->opts));
+                           sweep_cfg(P));
         MWI_CUDA(cudaStreamSynchronize(P->st));
+        check_sweep_error(P);
     });
 }
 

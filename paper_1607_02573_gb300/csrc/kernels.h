@@ -84,6 +84,13 @@ struct TileLists {
 
 struct FrontsDev {
     int64_t nfronts = 0;
+    // tensor-core sweeps (sweep_tc.cu): 128-row tiles whose a_off is the
+    // front's offset in the tiled panel store (floats), the per-front tiled
+    // offsets, and the (front, 32-row block) list of the packing kernel
+    TileLists tiles128;
+    DevBuf<int64_t> t_off;
+    DevBuf<int2> pack_blocks;
+    int64_t n_pack_blocks = 0, tiled_floats = 0;
     DevBuf<int32_t> start, p, u, parent, sub;
     DevBuf<int64_t> f_off, u_off, upd_row, sch_off;
     DevBuf<int32_t> child_ptr, child;
@@ -138,22 +145,39 @@ template <typename C>
 void factorize_fronts(const FrontsDev& F, const UpdateTiles& ut, const double2* Bvals, C* ws, C* const sch[2],
                       C* inv_tmp, int* perturbed, cudaStream_t st);
 
-// y = M^{-1} x; scratch: Y, Z [nloc][m], upd [upd_rows][m]; tc selects the
-// complex FP32 sweep engine (0 CUDA cores, 1 tensor cores 3xTF32, 2 tensor cores TF32)
+// Complex FP32 sweep engine: tc = 0 CUDA cores, 1 mma.sync 3xTF32, 2 mma.sync
+// TF32, 4 tcgen05 TF32 over the tiled panel store wt (err: the kernels'
+// bounded-wait error code, 0 = none)
+struct SweepCfg {
+    int tc = 0;
+    const float* wt = nullptr;
+    int* err = nullptr;
+};
+
+// y = M^{-1} x; scratch: Y, Z [nloc][m], upd [upd_rows][m]
 template <typename C>
 void oras_apply(const FrontsDev& F, const C* ws, const double2* x, double2* y, int m, C* Y, C* Z, C* upd,
-                cudaStream_t st, const float2* x32 = nullptr, float2* y32 = nullptr, int tc = 0);
+                cudaStream_t st, const float2* x32 = nullptr, float2* y32 = nullptr, const SweepCfg& sc = SweepCfg());
 
 template <typename C>
-void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, int tc, cudaStream_t st);
+void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, const SweepCfg& sc,
+                        cudaStream_t st);
 int sweep_tile_rows(bool fp32);
+
+// tensor-core sweeps (sweep_tc.cu)
+int64_t tiled_panel_floats(int p, int f);
+void pack_tiled(const int2* blocks, int64_t nblocks, const int64_t* f_off, const int64_t* t_off, const int32_t* P,
+                const int32_t* U, const float2* ws, float* wt, cudaStream_t st);
+void sweep_tc_level(bool backward, const TileDesc* tiles, int64_t ntiles, int m, const int32_t* urows,
+                    const int2* asm2, const float* wt, const float2* dinv, float2* Y, float2* Z, float2* upd,
+                    int* err, cudaStream_t st);
 
 // Allocation-free ORAS application (oras.cu): scratch from a fixed-size
 // file-scope device array of kOrasScratchBytes.
 static const size_t kOrasScratchBytes = (size_t)32 << 20;
 size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed);
 void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const double2* x, double2* y, int m,
-                        int64_t n, cudaStream_t st, int tc = 0);
+                        int64_t n, cudaStream_t st, const SweepCfg& sc = SweepCfg());
 
 // ---- nodal (P1) permittivity parameter (p1.cu)
 struct Topology;

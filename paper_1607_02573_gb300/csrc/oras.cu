@@ -55,12 +55,12 @@ __global__ void scatter_kernel(int64_t n, int m, const int64_t* __restrict__ own
 
 template <typename C, typename In, typename Out>
 static void oras_apply_impl(const FrontsDev& F, const C* ws, const In* x, Out* y, int m, C* Y, C* Z, C* upd,
-                            cudaStream_t st, int tc) {
+                            cudaStream_t st, const SweepCfg& sc) {
     const int th = 256;
     int64_t tot = F.nloc * m;
     gather_kernel<In, C><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(F.nloc, m, F.loc2glob.p, x, Y);
     MWI_CHECK_LAUNCH();
-    multifrontal_solve<C>(F, ws, Y, Z, upd, m, tc, st);
+    multifrontal_solve<C>(F, ws, Y, Z, upd, m, sc, st);
     // scatter into the global vector (n = own_ptr size - 1)
     const int64_t n = (int64_t)F.own_ptr.n - 1;
     tot = n * m;
@@ -71,15 +71,15 @@ static void oras_apply_impl(const FrontsDev& F, const C* ws, const In* x, Out* y
 
 template <typename C>
 void oras_apply(const FrontsDev& F, const C* ws, const double2* x, double2* y, int m, C* Y, C* Z, C* upd,
-                cudaStream_t st, const float2* x32, float2* y32, int tc) {
-    if (x32) oras_apply_impl<C, float2, float2>(F, ws, x32, y32, m, Y, Z, upd, st, tc);
-    else oras_apply_impl<C, double2, double2>(F, ws, x, y, m, Y, Z, upd, st, tc);
+                cudaStream_t st, const float2* x32, float2* y32, const SweepCfg& sc) {
+    if (x32) oras_apply_impl<C, float2, float2>(F, ws, x32, y32, m, Y, Z, upd, st, sc);
+    else oras_apply_impl<C, double2, double2>(F, ws, x, y, m, Y, Z, upd, st, sc);
 }
 
 template void oras_apply<float2>(const FrontsDev&, const float2*, const double2*, double2*, int, float2*, float2*,
-                                 float2*, cudaStream_t, const float2*, float2*, int);
+                                 float2*, cudaStream_t, const float2*, float2*, const SweepCfg&);
 template void oras_apply<double2>(const FrontsDev&, const double2*, const double2*, double2*, int, double2*,
-                                  double2*, double2*, cudaStream_t, const float2*, float2*, int);
+                                  double2*, double2*, cudaStream_t, const float2*, float2*, const SweepCfg&);
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the ORAS application.  Its scratch (the local
@@ -123,7 +123,7 @@ size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed) {
 }
 
 void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const double2* x, double2* y, int m,
-                        int64_t n, cudaStream_t st, int tc) {
+                        int64_t n, cudaStream_t st, const SweepCfg& sc) {
     const size_t need = oras_noalloc_bytes(F, n, m, mixed);
     if (need > kOrasScratchBytes)
         throw Error(MWI_EINVAL, "problem needs " + std::to_string(need) + " bytes of ORAS scratch; the "
@@ -141,12 +141,12 @@ void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const do
         convert_c128_to_c64(n * m, x, v32, st);
         oras_apply_impl<float2, float2, float2>(F, static_cast<const float2*>(ws), v32, x32, m,
                                                 reinterpret_cast<float2*>(Yp), reinterpret_cast<float2*>(Zp),
-                                                reinterpret_cast<float2*>(Up), st, tc);
+                                                reinterpret_cast<float2*>(Up), st, sc);
         convert_c64_to_c128(n * m, x32, y, st);
     } else {
         oras_apply_impl<double2, double2, double2>(F, static_cast<const double2*>(ws), x, y, m,
                                                    reinterpret_cast<double2*>(Yp), reinterpret_cast<double2*>(Zp),
-                                                   reinterpret_cast<double2*>(Up), st, 0);
+                                                   reinterpret_cast<double2*>(Up), st, SweepCfg());
     }
 }
 

@@ -501,20 +501,42 @@ static void launch_gather(const FrontsDev& F, int l, C* Y, const C* upd, int m, 
     MWI_CHECK_LAUNCH();
 }
 
+// one level's product on the fifth-generation tensor cores (sweep_tc.cu)
 template <typename C>
-void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, int tc, cudaStream_t st) {
-    const int nlev = (int)F.level_ptr.size() - 1;
-    for (int l = 0; l < nlev; ++l) {
-        launch_gather<C>(F, l, Y, upd, m, st);
-        launch_gemm<C, kFwd>(F, l, ws, Y, Z, upd, m, tc, st);
+static void launch_tc_product(const FrontsDev& F, int l, bool backward, const C* ws, C* Y, C* Z, C* upd, int m,
+                              const SweepCfg& sc, cudaStream_t st) {
+    if constexpr (std::is_same<C, float2>::value) {
+        const TileLists& T = F.tiles128;
+        const int64_t b = backward ? T.p_ptr[l] : T.f_ptr[l];
+        const int64_t e = backward ? T.p_ptr[l + 1] : T.f_ptr[l + 1];
+        sweep_tc_level(backward, (backward ? T.p_tiles.p : T.f_tiles.p) + b, e - b, m, F.urows.p, F.asm2.p, sc.wt,
+                       ws + F.ws_entries, Y, Z, upd, sc.err, st);
+    } else {
+        throw Error(MWI_EINVAL, "internal: tensor-core sweeps need complex FP32 factors");
     }
-    for (int l = nlev - 1; l >= 0; --l) launch_gemm<C, kBwd>(F, l, ws, Y, Z, upd, m, tc, st);
 }
 
-template void multifrontal_solve<float2>(const FrontsDev&, const float2*, float2*, float2*, float2*, int, int,
-                                         cudaStream_t);
-template void multifrontal_solve<double2>(const FrontsDev&, const double2*, double2*, double2*, double2*, int, int,
-                                          cudaStream_t);
+template <typename C>
+void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, const SweepCfg& sc,
+                        cudaStream_t st) {
+    const int nlev = (int)F.level_ptr.size() - 1;
+    const bool tc5 = sc.tc == 4;
+    MWI_REQUIRE(!tc5 || (sc.wt && sc.err), MWI_EINVAL, "internal: tensor-core sweeps without the tiled panels");
+    for (int l = 0; l < nlev; ++l) {
+        launch_gather<C>(F, l, Y, upd, m, st);
+        if (tc5) launch_tc_product<C>(F, l, false, ws, Y, Z, upd, m, sc, st);
+        else launch_gemm<C, kFwd>(F, l, ws, Y, Z, upd, m, sc.tc, st);
+    }
+    for (int l = nlev - 1; l >= 0; --l) {
+        if (tc5) launch_tc_product<C>(F, l, true, ws, Y, Z, upd, m, sc, st);
+        else launch_gemm<C, kBwd>(F, l, ws, Y, Z, upd, m, sc.tc, st);
+    }
+}
+
+template void multifrontal_solve<float2>(const FrontsDev&, const float2*, float2*, float2*, float2*, int,
+                                         const SweepCfg&, cudaStream_t);
+template void multifrontal_solve<double2>(const FrontsDev&, const double2*, double2*, double2*, double2*, int,
+                                          const SweepCfg&, cudaStream_t);
 
 int sweep_tile_rows(bool large) { return large ? 64 : 32; }
 

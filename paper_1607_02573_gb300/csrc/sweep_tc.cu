@@ -1,0 +1,510 @@
+// ORAS sweeps on the fifth-generation tensor cores (tcgen05, sm_103a): the
+// multifrontal forward and backward products of sweep.cu (the B_i^{-1} of
+// Eq. ORAS applied to m right-hand sides at once, Section 3), with the factor
+// panels streamed by bulk asynchronous copies into shared memory and the
+// products accumulated in tensor memory.
+//
+// Factor layout ("tiled panels", written once per factorisation by
+// pack_tiled_kernel).  A front's f x p partitioned-inverse panel
+// [L11^{-1}; -L21 L11^{-1}] is cut into atoms of 32 rows x 8 pivots; rows are
+// padded to a multiple of 32 and pivots to a multiple of 8 with zeros.  An
+// atom holds two 1 KB planes (real parts, then imaginary parts), each 8 lines
+// of 128 bytes: line r holds pivot 8 kb + r, and its 32 floats are the
+// atom's rows in the 128-byte swizzled order of the tensor cores (16-byte
+// chunk j stored at chunk j ^ r).  Atoms follow each other row block by row
+// block ([rb][kb][plane]), so
+//   - for the forward product (rows = front rows, K = pivots) the 8 lines are
+//     K and the 32 floats are M: an MN-major operand (128B swizzle, M chunks
+//     of 32 rows at the leading-byte offset);
+//   - for the backward product (rows = pivots, K = front rows, the transposed
+//     panel) the 8 lines are M and the 32 floats are K: a K-major operand
+//     (128B swizzle, groups of 8 pivots at the stride-byte offset),
+// and every stage of either product is one to four contiguous byte ranges,
+// copied with cp.async.bulk.
+//
+// Complex product as two real products.  With A = Ar + i Ai (the two planes)
+// and the right-hand sides B stored as reals [k][2c + (0 re, 1 im)], the MMA
+// computes Dr = Ar B and Di = Ai B (N = 64 real columns for 32 complex
+// columns, TF32 inputs -- the tensor core reads the FP32 bits and drops the
+// low 13 mantissa bits -- FP32 accumulation); then
+//   Re C(i, c) = Dr[i][2c] - Di[i][2c+1],  Im C(i, c) = Dr[i][2c+1] + Di[i][2c].
+//
+// Kernel: persistent, one CTA per SM, tiles (front, 128-row tile, 32-column
+// chunk) taken in a fixed stride.  Warp roles:
+//   warp 0      one lane issues the panel bulk copies (mbarrier transaction count)
+//   warp 1      owns the tensor memory (2 x 128 columns: accumulators double
+//               buffered across tiles); one lane issues tcgen05.mma and commits
+//   warps 2-5   gather the right-hand-side rows into the swizzled B stage
+//   warps 6-9   epilogue: tcgen05.ld, complex combine, D^{-1} scaling or
+//               extend-add of the children's update rows, global stores
+// Stages (4 x 40 KB) form a ring shared by all tiles of the CTA, so loads of
+// the next tile overlap the products and the epilogue of the current one.
+// Every wait is bounded: on expiry the kernel records an error code, the
+// other roles stop at their next wait, and the CTA frees its tensor memory
+// and returns.
+#include <algorithm>
+
+#include "common.h"
+#include "kernels.h"
+
+namespace mwi {
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kKS = 4;                      // pivot atoms (of 8) per forward stage
+constexpr int kAStage = 32768;              // forward 4 rb x 4 kb x 2 planes x 1 KB; backward 16 kb x 2 x 1 KB
+constexpr int kBStage = 8192;               // 32 K rows x 64 floats
+constexpr int kStage = kAStage + kBStage;
+constexpr int kThreads = 320;
+constexpr int kTmemCols = 256;
+constexpr int kSmemBytes = kStages * kStage + 1024 /* barriers */ + 1024 /* alignment */;
+constexpr long long kWaitLimit = 1ll << 24;
+
+enum { kFwdT = 0, kBwdT = 1 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait on a phase; false if the CTA aborts or the limit expires
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (it > 32) __nanosleep(64);
+    }
+    *abort_flag = 1;
+    atomicExch(err, code);
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: start, leading / stride byte offsets (>> 4),
+// version 1 (bit 46), 128-byte swizzle (layout type 2 at bits 61-63)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9, 10-12 = 2), A major (bit 15: 0 K, 1 MN), B MN-major (bit 16),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, int a_mn) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)a_mn << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Tile geometry shared by every role.  Forward: rows row0.. of the front
+// (M), K = pivots [0, k1) in atoms of 8, kKS atoms per stage.  Backward: rows
+// = pivots row0.., K = front rows from row0 (the panel is zero above its
+// diagonal) in row blocks of 32, one per stage.
+struct TcGeom {
+    int p, f, row0, Q, R, nst, nk;  // Q pivot atoms, R row blocks of the front; nst stages; nk atoms (fwd)
+};
+
+template <int MODE>
+__device__ __forceinline__ TcGeom tc_geom(const TileDesc& d) {
+    TcGeom g;
+    g.p = d.p;
+    g.f = d.f;
+    g.row0 = d.row0;
+    g.Q = (d.p + 7) >> 3;
+    g.R = (d.f + 31) >> 5;
+    if (MODE == kFwdT) {
+        const int k1 = min(d.p, d.row0 + 128);
+        g.nk = (k1 + 7) >> 3;
+        g.nst = (g.nk + kKS - 1) / kKS;
+    } else {
+        g.nk = 0;
+        g.nst = g.R - (d.row0 >> 5);
+    }
+    return g;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
+    const TileDesc* __restrict__ tiles, int ntiles, int nchunks, const int32_t* __restrict__ urows,
+    const int2* __restrict__ asm2, const float* __restrict__ wt, const float2* __restrict__ dinv,
+    float2* __restrict__ Y, float2* __restrict__ Z, float2* __restrict__ upd, int m, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStage);
+    // bars: full[kStages], empty[kStages], tfull[2], tempty[2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = smem_u32(smem);
+    auto full_bar = [&](int s) { return smem_u32(bars + s); };
+    auto empty_bar = [&](int s) { return smem_u32(bars + kStages + s); };
+    auto tfull_bar = [&](int b) { return smem_u32(bars + 2 * kStages + b); };
+    auto tempty_bar = [&](int b) { return smem_u32(bars + 2 * kStages + 2 + b); };
+
+    // stale shared memory must be finite: the MMA reads whole atoms, and the
+    // zero right-hand-side rows only cancel finite factor entries
+    for (int i = threadIdx.x; i < kStages * kStage / 16; i += kThreads)
+        reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full_bar(s), 1 + 4);  // the copy lane (with its transaction bytes) + 4 gather warps
+            mbar_init(empty_bar(s), 1);     // tcgen05.commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), 4);    // the 4 epilogue warps
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int total = ntiles * nchunks;
+
+    if (warp == 0) {
+        // ---------------- panel copies
+        if (lane == 0) {
+            long long g = 0;
+            bool ok = true;
+            for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x) {
+                const TileDesc d = tiles[ti / nchunks];
+                const TcGeom G = tc_geom<MODE>(d);
+                const float* P = wt + d.a_off;
+                for (int st = 0; st < G.nst && ok; ++st, ++g) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                    if (!(ok = mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 1))) break;
+                    const uint32_t a_dst = sbase + s * kStage;
+                    if (MODE == kFwdT) {
+                        const int kb0 = st * kKS, nk = min(kKS, G.nk - kb0);
+                        const int rb0 = d.row0 >> 5, nr = min(4, G.R - rb0);
+                        const uint32_t bytes = (uint32_t)nk * 2048u;
+                        mbar_arrive_tx(full_bar(s), bytes * nr);
+                        for (int r = 0; r < nr; ++r)
+                            bulk_g2s(a_dst + r * (kKS * 2048), P + ((int64_t)(rb0 + r) * G.Q + kb0) * 512, bytes,
+                                     full_bar(s));
+                    } else {
+                        const int rb = (d.row0 >> 5) + st, kb0 = d.row0 >> 3, nk = min(16, G.Q - kb0);
+                        const uint32_t bytes = (uint32_t)nk * 2048u;
+                        mbar_arrive_tx(full_bar(s), bytes);
+                        bulk_g2s(a_dst, P + ((int64_t)rb * G.Q + kb0) * 512, bytes, full_bar(s));
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- tensor-core products
+        if (lane == 0) {
+            long long g = 0;
+            int it = 0;
+            bool ok = true;
+            constexpr uint32_t kIdesc = idesc_tf32(128, 64, MODE == kFwdT ? 1 : 0);
+            for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x, ++it) {
+                const TileDesc d = tiles[ti / nchunks];
+                const TcGeom G = tc_geom<MODE>(d);
+                const int buf = it & 1;
+                if (!(ok = mbar_wait(tempty_bar(buf), ((it >> 1) & 1) ^ 1, abort_flag, err, 2))) break;
+                tc_fence_after();
+                const uint32_t dr = tmem + buf * 128, di = dr + 64;
+                for (int st = 0; st < G.nst; ++st, ++g) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                    if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, err, 3))) break;
+                    tc_fence_after();
+                    const uint32_t a0 = sbase + s * kStage, b0 = a0 + kAStage;
+                    if (MODE == kFwdT) {
+                        const int nk = min(kKS, G.nk - st * kKS);
+                        for (int kk = 0; kk < nk; ++kk) {
+                            const uint64_t bd = smem_desc(b0 + kk * 1024, 4096, 1024);
+                            const uint32_t acc = (st > 0 || kk > 0) ? 1u : 0u;
+                            mma_tf32(dr, smem_desc(a0 + kk * 2048, kKS * 2048, 1024), bd, kIdesc, acc);
+                            mma_tf32(di, smem_desc(a0 + kk * 2048 + 1024, kKS * 2048, 1024), bd, kIdesc, acc);
+                        }
+                    } else {
+                        for (int q = 0; q < 4; ++q) {
+                            const uint64_t bd = smem_desc(b0 + q * 1024, 4096, 1024);
+                            const uint32_t acc = (st > 0 || q > 0) ? 1u : 0u;
+                            mma_tf32(dr, smem_desc(a0 + q * 32, 16, 2048), bd, kIdesc, acc);
+                            mma_tf32(di, smem_desc(a0 + 1024 + q * 32, 16, 2048), bd, kIdesc, acc);
+                        }
+                    }
+                    mma_commit(empty_bar(s));
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar(buf));
+            }
+        }
+    } else if (warp < 6) {
+        // ---------------- right-hand-side rows into the B stage
+        const int pw = warp - 2;
+        long long g = 0;
+        bool ok = true;
+        for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x) {
+            const TileDesc d = tiles[ti / nchunks];
+            const TcGeom G = tc_geom<MODE>(d);
+            const int c = (ti % nchunks) * 32 + lane;
+            const bool cin = c < m;
+            const int32_t* ur = urows + d.u_off;
+            for (int st = 0; st < G.nst; ++st, ++g) {
+                const int s = (int)(g % kStages);
+                const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                if (!(ok = mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 4))) break;
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int r = pw * 8 + j;  // stage row (K index within the stage)
+                    float2 x = make_float2(0.f, 0.f);
+                    if (MODE == kFwdT) {
+                        const int k = st * kKS * 8 + r;
+                        if (cin && k < min(G.p, G.row0 + 128)) x = Y[(d.rowbase + k) * m + c];
+                    } else {
+                        const int i = (((d.row0 >> 5) + st) << 5) + r;
+                        if (cin) {
+                            if (i < G.p) x = Z[(d.rowbase + i) * m + c];
+                            else if (i < G.f) x = Y[(d.sbase + ur[i - G.p]) * m + c];
+                        }
+                    }
+                    v[j] = x;
+                }
+                unsigned char* B = smem + s * kStage + kAStage;
+                const int nc = lane >> 4, j16 = (lane & 15) >> 1, e = (lane & 1) * 8;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int r = pw * 8 + j, rr = r & 7;
+                    *reinterpret_cast<float2*>(B + nc * 4096 + (r >> 3) * 1024 + rr * 128 + ((j16 ^ rr) << 4) + e) =
+                        v[j];
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full_bar(s));
+            }
+        }
+    } else {
+        // ---------------- epilogue
+        const int lg = warp & 3;  // tensor-memory lane group of this warp
+        const int i = lg * 32 + lane;
+        int it = 0;
+        bool ok = true;
+        for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x, ++it) {
+            const TileDesc d = tiles[ti / nchunks];
+            const int c0 = (ti % nchunks) * 32;
+            const int buf = it & 1;
+            if (!(ok = mbar_wait(tfull_bar(buf), (it >> 1) & 1, abort_flag, err, 5))) break;
+            tc_fence_after();
+            float o[64];
+            const uint32_t t0 = tmem + ((uint32_t)(lg * 32) << 16) + buf * 128;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float dr[32], di[32];
+                tmem_ld32(t0 + h * 32, dr);
+                tmem_ld32(t0 + 64 + h * 32, di);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    o[32 * h + 2 * q] = dr[2 * q] - di[2 * q + 1];
+                    o[32 * h + 2 * q + 1] = dr[2 * q + 1] + di[2 * q];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(buf));
+            const int gi = d.row0 + i;
+            const int nc = min(32, m - c0);
+            float2* dst = nullptr;
+            if (MODE == kBwdT) {
+                if (gi < d.p) dst = Y + (d.rowbase + gi) * m + c0;
+            } else if (gi < d.p) {
+                const float2 dv = dinv[d.rowbase + gi];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const float re = o[2 * q], im = o[2 * q + 1];
+                    o[2 * q] = re * dv.x - im * dv.y;
+                    o[2 * q + 1] = re * dv.y + im * dv.x;
+                }
+                dst = Z + (d.rowbase + gi) * m + c0;
+            } else if (gi < d.f) {
+                const int2 src = asm2[d.asm_base + gi];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    if (q < nc) {
+                        if (src.x >= 0) {
+                            const float2 a = upd[(int64_t)src.x * m + c0 + q];
+                            o[2 * q] += a.x;
+                            o[2 * q + 1] += a.y;
+                        }
+                        if (src.y >= 0) {
+                            const float2 a = upd[(int64_t)src.y * m + c0 + q];
+                            o[2 * q] += a.x;
+                            o[2 * q + 1] += a.y;
+                        }
+                    }
+                }
+                dst = upd + (d.upd_row + gi - d.p) * m + c0;
+            }
+            if (dst) {
+                if (nc == 32 && (m & 1) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        reinterpret_cast<float4*>(dst)[q] =
+                            make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (q < nc) dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// One block per (front, 32-row block): the panel rows of the block for every
+// pivot atom, in the tiled, swizzled two-plane layout described above.
+__global__ void __launch_bounds__(256) pack_tiled_kernel(const int2* __restrict__ blocks,
+                                                         const int64_t* __restrict__ f_off,
+                                                         const int64_t* __restrict__ t_off,
+                                                         const int32_t* __restrict__ P, const int32_t* __restrict__ U,
+                                                         const float2* __restrict__ ws, float* __restrict__ wt) {
+    const int2 bl = blocks[blockIdx.x];  // (front, row block)
+    const int s = bl.x, rb = bl.y;
+    const int p = P[s], f = p + U[s];
+    const int Q = (p + 7) >> 3;
+    const float2* L = ws + f_off[s];
+    float* T = wt + t_off[s];
+    const int r = threadIdx.x >> 5, c = threadIdx.x & 31;  // line (pivot in atom), row in block
+    const int row = rb * 32 + c;
+    for (int kb = 0; kb < Q; ++kb) {
+        const int k = kb * 8 + r;
+        const float2 v = (k < p && row < f) ? L[(int64_t)k * f + row] : make_float2(0.f, 0.f);
+        float* atom = T + ((int64_t)rb * Q + kb) * 512;
+        const int pos = r * 32 + ((((c >> 2) ^ r) << 2) | (c & 3));
+        atom[pos] = v.x;
+        atom[256 + pos] = v.y;
+    }
+}
+
+}  // namespace
+
+int64_t tiled_panel_floats(int p, int f) { return (int64_t)((f + 31) / 32) * ((p + 7) / 8) * 512; }
+
+void pack_tiled(const int2* blocks, int64_t nblocks, const int64_t* f_off, const int64_t* t_off, const int32_t* P,
+                const int32_t* U, const float2* ws, float* wt, cudaStream_t st) {
+    for (int64_t b = 0; b < nblocks; b += 65535 * 64) {
+        const int64_t n = std::min<int64_t>(nblocks - b, 65535 * 64);
+        pack_tiled_kernel<<<(unsigned)n, 256, 0, st>>>(blocks + b, f_off, t_off, P, U, ws, wt);
+        MWI_CHECK_LAUNCH();
+    }
+}
+
+int sweep_tc_ctas() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, sms = 0;
+        MWI_CUDA(cudaGetDevice(&dev));
+        MWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        n = std::max(1, sms);
+    }
+    return n;
+}
+
+template <int MODE>
+static void launch_tc(const TileDesc* tiles, int64_t ntiles, int m, const int32_t* urows, const int2* asm2,
+                      const float* wt, const float2* dinv, float2* Y, float2* Z, float2* upd, int* err,
+                      cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        MWI_CUDA(cudaFuncSetAttribute(sweep_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kSmemBytes));
+        attr = true;
+    }
+    const int nchunks = (m + 31) / 32;
+    const int64_t total = ntiles * nchunks;
+    const int grid = (int)std::min<int64_t>(total, sweep_tc_ctas());
+    sweep_tc_kernel<MODE><<<grid, kThreads, kSmemBytes, st>>>(tiles, (int)ntiles, nchunks, urows, asm2, wt, dinv, Y,
+                                                              Z, upd, m, err);
+    MWI_CHECK_LAUNCH();
+}
+
+void sweep_tc_level(bool backward, const TileDesc* tiles, int64_t ntiles, int m, const int32_t* urows,
+                    const int2* asm2, const float* wt, const float2* dinv, float2* Y, float2* Z, float2* upd,
+                    int* err, cudaStream_t st) {
+    if (ntiles <= 0) return;
+    MWI_REQUIRE(ntiles * ((m + 31) / 32) < ((int64_t)1 << 31), MWI_EINVAL, "too many sweep tiles");
+    if (backward) launch_tc<kBwdT>(tiles, ntiles, m, urows, asm2, wt, dinv, Y, Z, upd, err, st);
+    else launch_tc<kFwdT>(tiles, ntiles, m, urows, asm2, wt, dinv, Y, Z, upd, err, st);
+}
+
+}  // namespace mwi
