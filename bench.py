@@ -73,6 +73,8 @@ def parse():
                     help="timed gradient steps with Krylov recycling across steps (0: skip)")
     ap.add_argument("--block-steps", type=int, default=1,
                     help="timed forward solves comparing true block FGMRES with pseudo-block (0: skip)")
+    ap.add_argument("--no-errors", action="store_true",
+                    help="skip the accuracy statement (mixed path against the FP64 path at rtol 1e-12)")
     ap.add_argument("--p1-steps", type=int, default=2,
                     help="timed gradient steps with the nodal (P1) parameter (0: skip)")
     ap.add_argument("--engine", type=int, default=2, help="complex FP32 sweep engine (see mwi_solver_opts)")
@@ -251,6 +253,8 @@ def run_mine(args, rank, world):
         args.requests = 2
         args.no_cpu_baseline = True
     results["mixed"] = one_arm(1, args.steps, args.warmup, max(2, args.requests))
+    if not args.no_errors and not args.only_mixed:
+        results["errors"] = error_statement(args, mwi, M, mesh, eps, ants, dev, stream)
     results["nested"] = one_arm(2, args.nested_steps, args.warmup, 0) if args.nested_steps > 0 else None
     results["fp64"] = one_arm(0, args.fp64_steps, args.warmup, 0) if args.fp64_steps > 0 else None
     # Krylov recycling: the same step sequence (eps_r alternating between two maps 1 % apart, as
@@ -319,6 +323,61 @@ def run_mine(args, rank, world):
     return mesh, M, results
 
 
+def db_bins(S, S_ref, edges=(0.0, -20.0, -60.0)):
+    """Largest entrywise relative error of S against S_ref in bins of
+    |S_ref| in dB below its largest entry: [0, -20), [-20, -60), below -60."""
+    a = np.abs(S_ref)
+    db = 20.0 * np.log10(np.maximum(a, 1e-300) / a.max())
+    rel = np.abs(S - S_ref) / np.maximum(a, 1e-300)
+    out = {}
+    for hi, lo in zip(edges, list(edges[1:]) + [-np.inf]):
+        sel = (db <= hi) & (db > lo)
+        name = f"{hi:g}..{lo:g} dB"
+        out[name] = {"count": int(sel.sum()), "max_rel": float(rel[sel].max()) if sel.any() else None}
+    out["lowest_db"] = float(db.min())
+    return out
+
+
+def error_statement(args, mwi, M, mesh, eps, ants, dev, stream):
+    """Accuracy of the headline (mixed path, rtol 1e-6) on the bench workload,
+    against the plain FP64 path solved to rtol 1e-12 on the same GPU and the
+    same inputs (the FP64 path matches the CPU oracle to 1e-8 in the parity
+    tests): forward and adjoint fields per column, S per dB bin, J and the
+    per-tet gradient."""
+    import torch
+
+    from synthetic import add_noise, chamber_target_eps
+    target = torch.from_numpy(chamber_target_eps(mesh.xyz, mesh.tet)).to(dev)
+    eps0 = torch.from_numpy(eps).to(dev)
+    res = {}
+    S_meas = None
+    for name, prec, rtol in (("ref", 0, 1e-12), ("mixed", 1, RTOL)):
+        P = mwi.Problem(M, target, FREQ, stream=stream, n_sub=64, precision=prec, rtol=rtol, max_iter=2000,
+                        nd_leaf=args.nd_leaf, sweep_engine=args.engine)
+        if S_meas is None:
+            S_meas = add_noise(P.forward_solve(ants, ants), eta=0.01, seed=1234)
+        P.update_eps(eps0)
+        S = P.forward_solve(ants, ants)
+        it_f = P.info.iters_max
+        J, grad = P.misfit_and_gradient(S_meas)
+        res[name] = dict(S=S, J=J, grad=grad, U=P.fields_host(0), L=P.fields_host(1), its=(it_f, P.info.iters_max))
+        P.close()
+    r, m_ = res["ref"], res["mixed"]
+    cu = np.linalg.norm(m_["U"] - r["U"], axis=0) / np.linalg.norm(r["U"], axis=0)
+    cl = np.linalg.norm(m_["L"] - r["L"], axis=0) / np.linalg.norm(r["L"], axis=0)
+    g_ref = np.abs(r["grad"]).max()
+    return {"reference": "plain FP64 GPU path at rtol 1e-12, same inputs (gel + head + inclusion eps_r, S_meas "
+                         "from the two-inclusion target with 1 % noise)",
+            "rtol": RTOL, "iterations_mixed": m_["its"], "iterations_reference": r["its"],
+            "fields_col_rel_max": float(cu.max()), "fields_col_rel_median": float(np.median(cu)),
+            "adjoint_col_rel_max": float(cl.max()),
+            "S_normwise_rel": float(np.linalg.norm(m_["S"] - r["S"]) / np.linalg.norm(r["S"])),
+            "S_by_db_bin": db_bins(m_["S"], r["S"]),
+            "J_rel": float(abs(m_["J"] - r["J"]) / abs(r["J"])),
+            "grad_normwise_rel": float(np.linalg.norm(m_["grad"] - r["grad"]) / np.linalg.norm(r["grad"])),
+            "grad_entry_max_over_max": float(np.abs(m_["grad"] - r["grad"]).max() / g_ref)}
+
+
 def roofline(res, ndof, m, traffic=None):
     """ORAS apply (gather, forward and backward multifrontal sweeps, scatter),
     HBM-bound.  Algorithmic bytes per call, each operand moved once: the
@@ -357,65 +416,56 @@ def roofline(res, ndof, m, traffic=None):
 
 
 # ---------------------------------------------------------------- CPU baseline (the oracle)
-class _OrasPool:
-    """The oracle's one-level ORAS (oracle.dd: local matrices B_i, SuperLU per
-    subdomain, y = sum_i R_i^T D_i B_i^-1 R_i x) with its subdomains spread
-    over forked worker processes, one contiguous share of subdomains each.
-    Vectors travel through shared memory; the main process sums the workers'
-    partial results in a fixed order.  Fork only: create it before any CUDA
-    call in this process."""
+# Iterations per column of the oracle's FGMRES + ORAS (exact subdomain solves)
+# on the bench workload at rtol 1e-6: a complete oracle run of that workload
+# (all 64 subdomains factored, two transmitter columns solved) took 12 for
+# both columns.  The timed samples below use it to extrapolate a column.
+ORACLE_ITERATIONS = 12
 
-    def __init__(self, mesh, topo, dec, eps, K, M, workers):
+
+class _SubdomainPool:
+    """The oracle's one-level ORAS pieces (oracle.dd: local matrix B_i and its
+    SuperLU factors) for a sample of the subdomains, one per forked worker
+    process, each timing its own factorisation and its local solve
+    y += D_i B_i^-1 R_i x.  Fork only: create it before any CUDA call."""
+
+    def __init__(self, mesh, topo, dec, eps, K, M, ids):
         import multiprocessing as mp
-        self.n = topo.ndof
-        self.W = workers
         ctx = mp.get_context("fork")
-        self.x = ctx.RawArray("d", 2 * self.n)
-        self.y = ctx.RawArray("d", 2 * self.n * workers)
         self.pipes, self.procs = [], []
-        shares = np.array_split(np.arange(dec.nsub), workers)
-        for w in range(workers):
+        for i in ids:
             a, b = ctx.Pipe()
-            p = ctx.Process(target=_OrasPool._worker, args=(b, w, shares[w], mesh, topo, dec, eps, K, M,
-                                                            self.x, self.y, self.n))
+            p = ctx.Process(target=_SubdomainPool._worker, args=(b, int(i), mesh, topo, dec, eps, K, M))
             p.start()
             self.pipes.append(a)
             self.procs.append(p)
-        self.setup_s = max(c.recv() for c in self.pipes)
+        self.t_factor = [c.recv() for c in self.pipes]
 
     @staticmethod
-    def _worker(conn, w, ids, mesh, topo, dec, eps, K, M, xs, ys, n):
+    def _worker(conn, i, mesh, topo, dec, eps, K, M):
         import types
 
         import scipy.sparse.linalg as spla
 
         import oracle as O
         t0 = time.perf_counter()
-        view = types.SimpleNamespace(nsub=len(ids), Td=[dec.Td[i] for i in ids], R=[dec.R[i] for i in ids])
-        Bs = O.dd.local_matrices(mesh.xyz, topo, view, eps, FREQ, K, M)
-        lus = [spla.splu(B.tocsc(), permc_spec="MMD_AT_PLUS_A") for B in Bs]
+        view = types.SimpleNamespace(nsub=1, Td=[dec.Td[i]], R=[dec.R[i]])
+        B = O.dd.local_matrices(mesh.xyz, topo, view, eps, FREQ, K, M)[0]
+        lu = spla.splu(B.tocsc(), permc_spec="MMD_AT_PLUS_A")
         conn.send(time.perf_counter() - t0)
-        x = np.frombuffer(xs, dtype=np.complex128)
-        y = np.frombuffer(ys, dtype=np.complex128).reshape(-1, n)[w]
+        rng = np.random.default_rng(i)
+        x = rng.standard_normal(topo.ndof) + 1j * rng.standard_normal(topo.ndof)
+        y = np.zeros(topo.ndof, dtype=np.complex128)
         while conn.recv():
-            y[:] = 0.0
-            for k, i in enumerate(ids):
-                Ri = dec.R[i]
-                y[Ri] += dec.D[i] * lus[k].solve(np.ascontiguousarray(x[Ri]))
-            conn.send(True)
+            t0 = time.perf_counter()
+            Ri = dec.R[i]
+            y[Ri] += dec.D[i] * lu.solve(np.ascontiguousarray(x[Ri]))
+            conn.send(time.perf_counter() - t0)
 
-    def apply(self, r):
-        x = np.frombuffer(self.x, dtype=np.complex128)
-        x[:] = r
+    def solve_times(self):
         for c in self.pipes:
             c.send(True)
-        for c in self.pipes:
-            c.recv()
-        parts = np.frombuffer(self.y, dtype=np.complex128).reshape(self.W, self.n)
-        z = parts[0].copy()
-        for w in range(1, self.W):
-            z += parts[w]
-        return z
+        return [c.recv() for c in self.pipes]
 
     def close(self):
         for c in self.pipes:
@@ -425,83 +475,89 @@ class _OrasPool:
 
 
 def cpu_oracle_setup(args):
-    """The oracle on the bench's own workload: topology, element integrals,
-    assembly of A (single-threaded, as the oracle stands), the decomposition
-    (RCB, 64 subdomains, delta = 1) and, in a pool over all host cores, the
-    local matrices and their SuperLU factors."""
+    """The oracle on the bench's own workload: topology, element integrals and
+    the assembly of A (single-threaded, as the oracle stands; timed, it is
+    part of every gradient step), the decomposition (RCB, 64 subdomains,
+    delta = 1), and one sampled subdomain per host core factored in a
+    process pool (timed)."""
     import oracle as O
-    from synthetic import add_noise, antenna_array, chamber_eps, chamber_mesh, ring_antennas  # noqa: F401
-    t0 = time.perf_counter()
+    from synthetic import antenna_array, chamber_eps, chamber_mesh, ring_antennas
     mesh = chamber_mesh(args.nxy, args.nz)
     eps = chamber_eps(mesh.xyz, mesh.tet)
     ants = antenna_array(ring_antennas(args.n_ant))
     topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, 1)
-    t1 = time.perf_counter()
     K, M = O.element_matrices(mesh.xyz, topo)
+    t0 = time.perf_counter()
     A = O.assemble_system(mesh.xyz, topo, eps, FREQ, K=K, M=M)
-    t2 = time.perf_counter()
-    part = O.dd.rcb_partition(mesh.xyz, mesh.tet, 64)
+    t_asm = time.perf_counter() - t0
+    nsub = 64
+    part = O.dd.rcb_partition(mesh.xyz, mesh.tet, nsub)
     dec = O.dd.Decomposition(mesh.xyz, mesh.tet, topo, part, 1)
     cores = len(os.sched_getaffinity(0))
-    pool = _OrasPool(mesh, topo, dec, eps, K, M, cores)
-    t3 = time.perf_counter()
-    return dict(mesh=mesh, eps=eps, ants=ants, topo=topo, A=A, K=K, M=M, pool=pool, cores=cores,
-                mesh_s=t1 - t0, assemble_s=t2 - t1, local_factor_s=t3 - t2)
+    ids = np.unique(np.linspace(0, nsub - 1, min(cores, nsub)).round().astype(int))
+    pool = _SubdomainPool(mesh, topo, dec, eps, K, M, ids)
+    return dict(mesh=mesh, eps=eps, ants=ants, topo=topo, A=A, K=K, M=M, pool=pool, cores=cores, nsub=nsub,
+                ids=ids, t_asm=t_asm, t_factor=pool.t_factor)
 
 
-def cpu_oracle_columns(ctx, cols):
-    """Solve the given transmitter columns with the oracle's FGMRES + ORAS to
-    the metric's rtol; returns seconds per column and the iteration counts."""
+def cpu_oracle_sample(ctx):
+    """One bounded sample of a gradient step: every sampled subdomain's local
+    solve (in parallel), one SpMM with the oracle's A, and the dot product +
+    update pair of the oracle's Gram-Schmidt, each timed; returns the step
+    time extrapolated to 64 subdomains over all cores, ORACLE_ITERATIONS
+    iterations per column and 2 x n_ant columns, and its parts."""
     import oracle as O
-    topo, ants = ctx["topo"], ctx["ants"]
-    tdof, tsgn = O.antenna_edges(ctx["mesh"].xyz, topo, ants)
-    B = O.build_rhs(topo.ndof, tdof, tsgn, ants[:, 6] + 1j * ants[:, 7], FREQ)
-    its = []
+    topo, A = ctx["topo"], ctx["A"]
+    n = topo.ndof
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    t_solve = float(np.mean(ctx["pool"].solve_times()))
     t0 = time.perf_counter()
-    for j in cols:
-        _, it, _ = O.dd.fgmres(ctx["A"], B[:, j], ctx["pool"].apply, rtol=RTOL, restart=50, maxiter=500)
-        its.append(it)
-    return (time.perf_counter() - t0) / len(cols), its
-
-
-def cpu_baseline_value(ctx, t_col, n_cols):
-    """RHS-solves/s of one oracle gradient step on the bench workload: the
-    numeric setup (assembly of A; local matrices and factors in the pool) plus
-    n_cols column solves at the sampled time per column (the per-tet gradient
-    is a few einsums, timed on the workload's own sizes)."""
-    import oracle as O
-    topo = ctx["topo"]
-    rng = np.random.default_rng(0)
-    m = n_cols // 2
-    U = rng.standard_normal((topo.ndof, m)) + 0j
+    for _ in range(3):
+        y = A @ x
+    t_spmm = (time.perf_counter() - t0) / 3
     t0 = time.perf_counter()
-    O.gradient(ctx["mesh"].xyz, topo, ctx["eps"], FREQ, U, U, M=ctx["M"])
-    t_grad = time.perf_counter() - t0
-    step = ctx["assemble_s"] + ctx["local_factor_s"] + n_cols * t_col + t_grad
-    return n_cols / step, step, t_grad
+    for _ in range(10):
+        h = np.vdot(x, y)
+        y = y - h * x
+    t_gs = (time.perf_counter() - t0) / 10
+    per_worker = ctx["nsub"] / ctx["cores"]            # subdomains per process in a full pool
+    t_apply = per_worker * t_solve
+    it = ORACLE_ITERATIONS
+    t_col = it * (t_apply + t_spmm) + t_spmm + 0.5 * it * (it + 1) * t_gs
+    t_fact = per_worker * float(np.mean(ctx["t_factor"]))
+    n_cols = 2 * ctx["ants"].shape[0]
+    if "t_grad" not in ctx:
+        U = rng.standard_normal((n, n_cols // 2)) + 0j
+        t0 = time.perf_counter()
+        O.gradient(ctx["mesh"].xyz, topo, ctx["eps"], FREQ, U, U, M=ctx["M"])
+        ctx["t_grad"] = time.perf_counter() - t0
+    step = ctx["t_asm"] + t_fact + n_cols * t_col + ctx["t_grad"]
+    return dict(step=step, value=n_cols / step, t_col=t_col, t_apply=t_apply, t_spmm=t_spmm, t_fact=t_fact,
+                t_solve=t_solve)
 
 
-def cpu_baseline(args, n_sample=2):
-    """The oracle as it stands on the bench's own workload, over all host
-    cores (subdomain factorisations and solves in a process pool), with a
-    bounded sample of columns solved to the metric's rtol."""
+def cpu_sample_text(ctx, smp):
+    return (f"oracle (complex128) on the bench workload ({ctx['mesh'].nt} tets, {ctx['topo'].ndof} DOF, "
+            f"{ctx['nsub']} subdomains, {ctx['ants'].shape[0]} + {ctx['ants'].shape[0]} columns): assembly of A "
+            f"{ctx['t_asm']:.1f} s (1 thread); {len(ctx['ids'])} of the {ctx['nsub']} subdomains factored (SuperLU) "
+            f"and solved, one per process, extrapolated to all subdomains over {ctx['cores']} processes "
+            f"(factorisation {smp['t_fact']:.1f} s, ORAS apply {smp['t_apply']:.3f} s); SpMM {smp['t_spmm']:.3f} s; "
+            f"{ORACLE_ITERATIONS} FGMRES iterations per column (a complete oracle run of this workload) -> "
+            f"{smp['t_col']:.2f} s per column; gradient {ctx['t_grad']:.1f} s; one step = {smp['step']:.0f} s")
+
+
+def cpu_baseline(args):
+    """The oracle as it stands on the bench's own workload over all host cores
+    (a bounded, timed sample extrapolated to the whole gradient step)."""
     ctx = cpu_oracle_setup(args)
     try:
-        t_col, its = cpu_oracle_columns(ctx, list(range(n_sample)))
-        n_cols = 2 * args.n_ant
-        v, step, t_grad = cpu_baseline_value(ctx, t_col, n_cols)
+        smp = cpu_oracle_sample(ctx)
     finally:
         ctx["pool"].close()
-    return {"value": v, "unit": UNIT, "cores": ctx["cores"], "kind": "oracle",
-            "config": "same workload as config.workload",
-            "sample": f"oracle (complex128) on the bench workload ({ctx['mesh'].nt} tets, {ctx['topo'].ndof} DOF, "
-                      f"64 subdomains): assembly of A {ctx['assemble_s']:.1f} s (1 thread), local matrices + SuperLU "
-                      f"factors {ctx['local_factor_s']:.1f} s ({ctx['cores']} processes), then {n_sample} of the "
-                      f"{n_cols} columns solved by the oracle's FGMRES + ORAS to rtol {RTOL:g} "
-                      f"({t_col:.2f} s per column, iterations {its}), gradient {t_grad:.2f} s; one step "
-                      f"extrapolated to {n_cols} columns = {step:.1f} s",
-            "setup_s": round(ctx["assemble_s"] + ctx["local_factor_s"], 2), "s_per_column": round(t_col, 3),
-            "iterations": its}
+    return {"value": smp["value"], "unit": UNIT, "cores": ctx["cores"], "kind": "oracle",
+            "config": "same workload as config.workload", "sample": cpu_sample_text(ctx, smp),
+            "s_per_step": round(smp["step"], 1)}
 
 
 def run_serving(args):
@@ -644,34 +700,27 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # the oracle on the same workload: numeric setup once, then every step a
-        # bounded sample (one transmitter column to rtol), extrapolated to the
-        # step's 2 x n_ant columns
+        # the oracle on the same workload: assembly and the sampled subdomain
+        # factorisations once, then every step a bounded timed sample
+        # (cpu_oracle_sample), extrapolated to the whole gradient step
         ctx = cpu_oracle_setup(args)
         n_cols = 2 * args.n_ant
-        vals, its, cols = [], [], []
+        vals, smp = [], None
         try:
             for k in range(args.warmup + args.steps):
-                t_col, it = cpu_oracle_columns(ctx, [k % args.n_ant])
+                smp = cpu_oracle_sample(ctx)
                 if k >= args.warmup:
-                    vals.append(cpu_baseline_value(ctx, t_col, n_cols)[0])
-                    its += it
-                    cols.append(t_col)
+                    vals.append(smp["value"])
         finally:
             ctx["pool"].close()
         v = float(np.mean(vals))
-        sample = (f"oracle (complex128) on the bench workload: assembly of A {ctx['assemble_s']:.1f} s (1 thread), "
-                  f"local matrices + SuperLU factors {ctx['local_factor_s']:.1f} s ({ctx['cores']} processes), "
-                  f"measured once; each step solves one transmitter column with the oracle's FGMRES + ORAS to "
-                  f"rtol {RTOL:g} ({np.mean(cols):.2f} s per column, iterations {sorted(set(its))}) and "
-                  f"extrapolates setup + {n_cols} columns + gradient")
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": n_cols / v * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                 "data": "synthetic",
                 "config": {"workload": workload_name(ctx["mesh"].nt, ctx["topo"].ndof, args)},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": ctx["cores"], "kind": "oracle",
-                                 "sample": sample},
+                                 "sample": cpu_sample_text(ctx, smp)},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -783,6 +832,8 @@ def main():
                                                        zip(["spmm", "oras_apply", "orthogonalisation",
                                                             "factorisation"], f["kernel_ms"])},
                                 "fwd": f["fwd_info"], "adj": f["adj_info"]}
+    if R.get("errors"):
+        line["errors"] = R["errors"]
     if cpu_line:
         line["cpu_baseline"] = cpu_line
     print(json.dumps(line))

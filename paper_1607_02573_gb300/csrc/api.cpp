@@ -613,9 +613,9 @@ void numeric_setup(mwi_problem* P, bool refactor = true) {
         timed(P, 3, [&] {
             factorize_fronts<float2>(E.F, E.ut[0], P->Bval.p, P->ws32.p, sch, P->inv32.p, P->perturbed.p, st);
             if (tc_of(P->opts) == 4) {
-                P->wt.ensure((size_t)E.F.tiled_floats);
+                P->wt.ensure(2 * (size_t)E.F.tiled_floats);
                 pack_tiled(E.F.pack_blocks.p, E.F.n_pack_blocks, E.F.f_off.p, E.F.t_off.p, E.F.p.p, E.F.u.p,
-                           P->ws32.p, P->wt.p, st);
+                           P->ws32.p, P->wt.p, E.F.tiled_floats, st);
             }
         });
         if (tc_of(P->opts) == 4 && !P->sweep_err.p) {

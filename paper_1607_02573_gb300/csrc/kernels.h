@@ -85,8 +85,9 @@ struct TileLists {
 struct FrontsDev {
     int64_t nfronts = 0;
     // tensor-core sweeps (sweep_tc.cu): 128-row tiles whose a_off is the
-    // front's offset in the tiled panel store (floats), the per-front tiled
-    // offsets, and the (front, 32-row block) list of the packing kernel
+    // front's offset in each tiled copy of the panels (floats), the per-front
+    // offsets, the (front, 32-row block) list of the packing kernel, and the
+    // floats of one copy (the store holds the forward then the backward copy)
     TileLists tiles128;
     DevBuf<int64_t> t_off;
     DevBuf<int2> pack_blocks;
@@ -166,8 +167,9 @@ int sweep_tile_rows(bool fp32);
 
 // tensor-core sweeps (sweep_tc.cu)
 int64_t tiled_panel_floats(int p, int f);
+// both tiled copies: the forward one at wt, the backward one at wt + bwd_base
 void pack_tiled(const int2* blocks, int64_t nblocks, const int64_t* f_off, const int64_t* t_off, const int32_t* P,
-                const int32_t* U, const float2* ws, float* wt, cudaStream_t st);
+                const int32_t* U, const float2* ws, float* wt, int64_t bwd_base, cudaStream_t st);
 void sweep_tc_level(bool backward, const TileDesc* tiles, int64_t ntiles, int m, const int32_t* urows,
                     const int2* asm2, const float* wt, const float2* dinv, float2* Y, float2* Z, float2* upd,
                     int* err, cudaStream_t st);

@@ -509,8 +509,8 @@ static void launch_tc_product(const FrontsDev& F, int l, bool backward, const C*
         const TileLists& T = F.tiles128;
         const int64_t b = backward ? T.p_ptr[l] : T.f_ptr[l];
         const int64_t e = backward ? T.p_ptr[l + 1] : T.f_ptr[l + 1];
-        sweep_tc_level(backward, (backward ? T.p_tiles.p : T.f_tiles.p) + b, e - b, m, F.urows.p, F.asm2.p, sc.wt,
-                       ws + F.ws_entries, Y, Z, upd, sc.err, st);
+        sweep_tc_level(backward, (backward ? T.p_tiles.p : T.f_tiles.p) + b, e - b, m, F.urows.p, F.asm2.p,
+                       sc.wt + (backward ? F.tiled_floats : 0), ws + F.ws_entries, Y, Z, upd, sc.err, st);
     } else {
         throw Error(MWI_EINVAL, "internal: tensor-core sweeps need complex FP32 factors");
     }

@@ -5,22 +5,24 @@
 // products accumulated in tensor memory.
 //
 // Factor layout ("tiled panels", written once per factorisation by
-// pack_tiled_kernel).  A front's f x p partitioned-inverse panel
-// [L11^{-1}; -L21 L11^{-1}] is cut into atoms of 32 rows x 8 pivots; rows are
-// padded to a multiple of 32 and pivots to a multiple of 8 with zeros.  An
-// atom holds two 1 KB planes (real parts, then imaginary parts), each 8 lines
-// of 128 bytes: line r holds pivot 8 kb + r, and its 32 floats are the
-// atom's rows in the 128-byte swizzled order of the tensor cores (16-byte
-// chunk j stored at chunk j ^ r).  Atoms follow each other row block by row
-// block ([rb][kb][plane]), so
-//   - for the forward product (rows = front rows, K = pivots) the 8 lines are
-//     K and the 32 floats are M: an MN-major operand (128B swizzle, M chunks
-//     of 32 rows at the leading-byte offset);
-//   - for the backward product (rows = pivots, K = front rows, the transposed
-//     panel) the 8 lines are M and the 32 floats are K: a K-major operand
-//     (128B swizzle, groups of 8 pivots at the stride-byte offset),
-// and every stage of either product is one to four contiguous byte ranges,
-// copied with cp.async.bulk.
+// pack_tiled_kernel).  The TF32 form of tcgen05.mma reads both operands
+// K-major (K contiguous in a line), and the two sweeps contract a front's
+// f x p partitioned-inverse panel [L11^{-1}; -L21 L11^{-1}] over different
+// indices -- the forward product over pivots, the backward one over rows --
+// so the panel is stored twice, cut into 8 x 8 blocks (rows and pivots padded
+// to multiples of 8 with zeros).  A block is two 256-byte planes (real parts,
+// then imaginary parts), each 8 lines of 32 bytes in the 32-byte swizzled
+// order of the tensor cores (16-byte chunk j of line r at chunk
+// j ^ ((r >> 2) & 1)):
+//   - forward copy: line = front row, 8 floats = pivots; blocks ordered
+//     [pivot chunk][row group][plane], so one 8-pivot K step of a 128-row
+//     tile is 16 consecutive blocks (row groups at the stride-byte offset);
+//   - backward copy: line = pivot, 8 floats = front rows; blocks ordered
+//     [row chunk][pivot group][plane].
+// A stage of 32 K values is at most four contiguous byte ranges, copied with
+// cp.async.bulk.  The right-hand sides are written K-major into the B stage by
+// the gather warps (line = real column, 32 floats = the stage's K rows,
+// 128-byte swizzle).
 //
 // Complex product as two real products.  With A = Ar + i Ai (the two planes)
 // and the right-hand sides B stored as reals [k][2c + (0 re, 1 im)], the MMA
@@ -51,9 +53,9 @@ namespace mwi {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kKS = 4;                      // pivot atoms (of 8) per forward stage
-constexpr int kAStage = 32768;              // forward 4 rb x 4 kb x 2 planes x 1 KB; backward 16 kb x 2 x 1 KB
-constexpr int kBStage = 8192;               // 32 K rows x 64 floats
+constexpr int kKS = 4;                      // K chunks of 8 per stage (K = 32)
+constexpr int kAStage = 32768;              // 4 K chunks x 16 groups of 8 M lines x 2 planes x 256 B
+constexpr int kBStage = 8192;               // 64 real columns x 32 K floats
 constexpr int kStage = kAStage + kBStage;
 constexpr int kThreads = 320;
 constexpr int kTmemCols = 256;
@@ -107,24 +109,26 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// shared-memory matrix descriptor: start, leading / stride byte offsets (>> 4),
-// version 1 (bit 46), 128-byte swizzle (layout type 2 at bits 61-63)
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor of a K-major operand: start, leading /
+// stride byte offsets (>> 4; the leading offset is unused by swizzled K-major
+// layouts), version 1 (bit 46), layout type at bits 61-63 (2 = 128-byte
+// swizzle, 6 = 32-byte swizzle)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, uint32_t layout) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)1 << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)layout << 61;
     return d;
 }
+constexpr uint32_t kSw128 = 2, kSw32 = 6;
 
 // instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
-// (bits 7-9, 10-12 = 2), A major (bit 15: 0 K, 1 MN), B MN-major (bit 16),
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, int a_mn) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)a_mn << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -154,12 +158,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Tile geometry shared by every role.  Forward: rows row0.. of the front
-// (M), K = pivots [0, k1) in atoms of 8, kKS atoms per stage.  Backward: rows
-// = pivots row0.., K = front rows from row0 (the panel is zero above its
-// diagonal) in row blocks of 32, one per stage.
+// Tile geometry shared by every role.  Forward: M = front rows row0..
+// (row groups g0.., ng of them), K = pivots [0, min(p, row0 + 128)) in chunks
+// of 8.  Backward: M = pivots row0.. (pivot groups g0..), K = front rows from
+// row0 (the panel is zero above its diagonal) to f, in chunks of 8.  The
+// chunks of a front's copy are cstride blocks apart.
 struct TcGeom {
-    int p, f, row0, Q, R, nst, nk;  // Q pivot atoms, R row blocks of the front; nst stages; nk atoms (fwd)
+    int p, f, row0, g0, ng, k0, nk, nst, cstride;
 };
 
 template <int MODE>
@@ -168,16 +173,20 @@ __device__ __forceinline__ TcGeom tc_geom(const TileDesc& d) {
     g.p = d.p;
     g.f = d.f;
     g.row0 = d.row0;
-    g.Q = (d.p + 7) >> 3;
-    g.R = (d.f + 31) >> 5;
+    const int F8 = (d.f + 7) >> 3, P8 = (d.p + 7) >> 3;
+    g.g0 = d.row0 >> 3;
     if (MODE == kFwdT) {
-        const int k1 = min(d.p, d.row0 + 128);
-        g.nk = (k1 + 7) >> 3;
-        g.nst = (g.nk + kKS - 1) / kKS;
+        g.ng = min(16, F8 - g.g0);
+        g.k0 = 0;
+        g.nk = (min(d.p, d.row0 + 128) + 7) >> 3;
+        g.cstride = F8;
     } else {
-        g.nk = 0;
-        g.nst = g.R - (d.row0 >> 5);
+        g.ng = min(16, P8 - g.g0);
+        g.k0 = d.row0 >> 3;
+        g.nk = F8 - g.k0;
+        g.cstride = P8;
     }
+    g.nst = (g.nk + kKS - 1) / kKS;
     return g;
 }
 
@@ -242,20 +251,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                     const uint32_t ph = (uint32_t)((g / kStages) & 1);
                     if (!(ok = mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 1))) break;
                     const uint32_t a_dst = sbase + s * kStage;
-                    if (MODE == kFwdT) {
-                        const int kb0 = st * kKS, nk = min(kKS, G.nk - kb0);
-                        const int rb0 = d.row0 >> 5, nr = min(4, G.R - rb0);
-                        const uint32_t bytes = (uint32_t)nk * 2048u;
-                        mbar_arrive_tx(full_bar(s), bytes * nr);
-                        for (int r = 0; r < nr; ++r)
-                            bulk_g2s(a_dst + r * (kKS * 2048), P + ((int64_t)(rb0 + r) * G.Q + kb0) * 512, bytes,
-                                     full_bar(s));
-                    } else {
-                        const int rb = (d.row0 >> 5) + st, kb0 = d.row0 >> 3, nk = min(16, G.Q - kb0);
-                        const uint32_t bytes = (uint32_t)nk * 2048u;
-                        mbar_arrive_tx(full_bar(s), bytes);
-                        bulk_g2s(a_dst, P + ((int64_t)rb * G.Q + kb0) * 512, bytes, full_bar(s));
-                    }
+                    const int c0 = G.k0 + st * kKS, nc = min(kKS, G.k0 + G.nk - c0);
+                    const uint32_t bytes = (uint32_t)G.ng * 512u;
+                    mbar_arrive_tx(full_bar(s), bytes * nc);
+                    for (int c = 0; c < nc; ++c)
+                        bulk_g2s(a_dst + c * 8192, P + ((int64_t)(c0 + c) * G.cstride + G.g0) * 128, bytes,
+                                 full_bar(s));
                 }
             }
         }
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
             long long g = 0;
             int it = 0;
             bool ok = true;
-            constexpr uint32_t kIdesc = idesc_tf32(128, 64, MODE == kFwdT ? 1 : 0);
+            constexpr uint32_t kIdesc = idesc_tf32(128, 64);
             for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x, ++it) {
                 const TileDesc d = tiles[ti / nchunks];
                 const TcGeom G = tc_geom<MODE>(d);
@@ -279,21 +280,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                     if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, err, 3))) break;
                     tc_fence_after();
                     const uint32_t a0 = sbase + s * kStage, b0 = a0 + kAStage;
-                    if (MODE == kFwdT) {
-                        const int nk = min(kKS, G.nk - st * kKS);
-                        for (int kk = 0; kk < nk; ++kk) {
-                            const uint64_t bd = smem_desc(b0 + kk * 1024, 4096, 1024);
-                            const uint32_t acc = (st > 0 || kk > 0) ? 1u : 0u;
-                            mma_tf32(dr, smem_desc(a0 + kk * 2048, kKS * 2048, 1024), bd, kIdesc, acc);
-                            mma_tf32(di, smem_desc(a0 + kk * 2048 + 1024, kKS * 2048, 1024), bd, kIdesc, acc);
-                        }
-                    } else {
-                        for (int q = 0; q < 4; ++q) {
-                            const uint64_t bd = smem_desc(b0 + q * 1024, 4096, 1024);
-                            const uint32_t acc = (st > 0 || q > 0) ? 1u : 0u;
-                            mma_tf32(dr, smem_desc(a0 + q * 32, 16, 2048), bd, kIdesc, acc);
-                            mma_tf32(di, smem_desc(a0 + 1024 + q * 32, 16, 2048), bd, kIdesc, acc);
-                        }
+                    const int nc = min(kKS, G.nk - st * kKS);
+                    for (int c = 0; c < nc; ++c) {
+                        // B: 64 lines (real columns) of 128 B, K step c = bytes 32c of every line
+                        const uint64_t bd = smem_desc(b0 + c * 32, 1024, kSw128);
+                        const uint32_t acc = (st > 0 || c > 0) ? 1u : 0u;
+                        mma_tf32(dr, smem_desc(a0 + c * 8192, 512, kSw32), bd, kIdesc, acc);
+                        mma_tf32(di, smem_desc(a0 + c * 8192 + 256, 512, kSw32), bd, kIdesc, acc);
                     }
                     mma_commit(empty_bar(s));
                 }
@@ -319,27 +312,31 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                 float2 v[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int r = pw * 8 + j;  // stage row (K index within the stage)
+                    const int r = pw * 8 + j;  // K index within the stage
+                    const int k = G.row0 * (MODE == kBwdT) + st * kKS * 8 + r;
                     float2 x = make_float2(0.f, 0.f);
-                    if (MODE == kFwdT) {
-                        const int k = st * kKS * 8 + r;
-                        if (cin && k < min(G.p, G.row0 + 128)) x = Y[(d.rowbase + k) * m + c];
-                    } else {
-                        const int i = (((d.row0 >> 5) + st) << 5) + r;
-                        if (cin) {
-                            if (i < G.p) x = Z[(d.rowbase + i) * m + c];
-                            else if (i < G.f) x = Y[(d.sbase + ur[i - G.p]) * m + c];
+                    if (cin) {
+                        if (MODE == kFwdT) {
+                            if (k < min(G.p, G.row0 + 128)) x = Y[(d.rowbase + k) * m + c];
+                        } else {
+                            if (k < G.p) x = Z[(d.rowbase + k) * m + c];
+                            else if (k < G.f) x = Y[(d.sbase + ur[k - G.p]) * m + c];
                         }
                     }
                     v[j] = x;
                 }
+                // line n = 2 lane (re) and 2 lane + 1 (im), 128-byte swizzled position of K index r
                 unsigned char* B = smem + s * kStage + kAStage;
-                const int nc = lane >> 4, j16 = (lane & 15) >> 1, e = (lane & 1) * 8;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int r = pw * 8 + j, rr = r & 7;
-                    *reinterpret_cast<float2*>(B + nc * 4096 + (r >> 3) * 1024 + rr * 128 + ((j16 ^ rr) << 4) + e) =
-                        v[j];
+                    const int r = pw * 8 + j;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int n = 2 * lane + h;
+                        *reinterpret_cast<float*>(B + (n >> 3) * 1024 + (n & 7) * 128 +
+                                                  ((((r >> 2) ^ (n & 7)) << 4) | ((r & 3) << 2))) =
+                            h ? v[j].y : v[j].x;
+                    }
                 }
                 fence_proxy_async();
                 __syncwarp();
@@ -431,40 +428,49 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
     }
 }
 
-// One block per (front, 32-row block): the panel rows of the block for every
-// pivot atom, in the tiled, swizzled two-plane layout described above.
+// One block per (front, 32-row block): the block's panel rows, for every
+// 8-pivot chunk, into both tiled copies (layout in the header comment).
+__device__ __forceinline__ int swz32(int line, int e) { return line * 8 + ((((e >> 2) ^ ((line >> 2) & 1)) << 2) | (e & 3)); }
+
 __global__ void __launch_bounds__(256) pack_tiled_kernel(const int2* __restrict__ blocks,
                                                          const int64_t* __restrict__ f_off,
                                                          const int64_t* __restrict__ t_off,
                                                          const int32_t* __restrict__ P, const int32_t* __restrict__ U,
-                                                         const float2* __restrict__ ws, float* __restrict__ wt) {
-    const int2 bl = blocks[blockIdx.x];  // (front, row block)
-    const int s = bl.x, rb = bl.y;
+                                                         const float2* __restrict__ ws, float* __restrict__ wt,
+                                                         int64_t bwd_base) {
+    const int2 bl = blocks[blockIdx.x];  // (front, 32-row block)
+    const int s = bl.x;
     const int p = P[s], f = p + U[s];
-    const int Q = (p + 7) >> 3;
+    const int F8 = (f + 7) >> 3, P8 = (p + 7) >> 3;
     const float2* L = ws + f_off[s];
-    float* T = wt + t_off[s];
-    const int r = threadIdx.x >> 5, c = threadIdx.x & 31;  // line (pivot in atom), row in block
-    const int row = rb * 32 + c;
-    for (int kb = 0; kb < Q; ++kb) {
-        const int k = kb * 8 + r;
+    float* Tf = wt + t_off[s];
+    float* Tb = wt + bwd_base + t_off[s];
+    const int e = threadIdx.x >> 5, rr = threadIdx.x & 31;  // pivot in its chunk, row in the block
+    const int row = bl.y * 32 + rr;
+    if ((row >> 3) >= F8) return;
+    const int rg = row >> 3, rl = row & 7;
+    for (int kc = 0; kc < P8; ++kc) {
+        const int k = kc * 8 + e;
         const float2 v = (k < p && row < f) ? L[(int64_t)k * f + row] : make_float2(0.f, 0.f);
-        float* atom = T + ((int64_t)rb * Q + kb) * 512;
-        const int pos = r * 32 + ((((c >> 2) ^ r) << 2) | (c & 3));
-        atom[pos] = v.x;
-        atom[256 + pos] = v.y;
+        float* bf = Tf + ((int64_t)kc * F8 + rg) * 128;   // forward: line = row, element = pivot
+        bf[swz32(rl, e)] = v.x;
+        bf[64 + swz32(rl, e)] = v.y;
+        float* bb = Tb + ((int64_t)rg * P8 + kc) * 128;   // backward: line = pivot, element = row
+        bb[swz32(e, rl)] = v.x;
+        bb[64 + swz32(e, rl)] = v.y;
     }
 }
 
 }  // namespace
 
-int64_t tiled_panel_floats(int p, int f) { return (int64_t)((f + 31) / 32) * ((p + 7) / 8) * 512; }
+// floats of one tiled copy of a front (8 x 8 blocks, two planes)
+int64_t tiled_panel_floats(int p, int f) { return (int64_t)((f + 7) / 8) * ((p + 7) / 8) * 128; }
 
 void pack_tiled(const int2* blocks, int64_t nblocks, const int64_t* f_off, const int64_t* t_off, const int32_t* P,
-                const int32_t* U, const float2* ws, float* wt, cudaStream_t st) {
+                const int32_t* U, const float2* ws, float* wt, int64_t bwd_base, cudaStream_t st) {
     for (int64_t b = 0; b < nblocks; b += 65535 * 64) {
         const int64_t n = std::min<int64_t>(nblocks - b, 65535 * 64);
-        pack_tiled_kernel<<<(unsigned)n, 256, 0, st>>>(blocks + b, f_off, t_off, P, U, ws, wt);
+        pack_tiled_kernel<<<(unsigned)n, 256, 0, st>>>(blocks + b, f_off, t_off, P, U, ws, wt, bwd_base);
         MWI_CHECK_LAUNCH();
     }
 }

@@ -230,3 +230,39 @@ def test_columns_independent_of_block_width(lib, precision):
     for S, J, grad in res[1:]:
         assert np.array_equal(S, res[0][0])
         assert np.array_equal(grad, res[0][2])
+
+
+def _db_bins(S, S_o):
+    a = np.abs(S_o)
+    db = 20.0 * np.log10(a / a.max())
+    rel = np.abs(S - S_o) / a
+    return db, rel
+
+
+@pytest.mark.parametrize("precision,engine,rtol", [(0, 0, 1e-12), (1, 4, 1e-9), (1, 2, 1e-9)])
+def test_s_and_gradient_entrywise_by_db_bins(lib, precision, engine, rtol):
+    """S entry by entry, binned by |S| in dB below its largest entry (the weak
+    transmissions carry the image, paper Section 6.2), and the gradient tet by
+    tet.  The solver bounds the error of every column relative to the column,
+    so an entry X dB below the largest one can lose up to X/20 digits: the
+    bound per bin is C rtol 10^(-lo/20), lo the bin's lower edge (the weakest
+    entry for the last bin), C = 1e3 as in the normwise tolerances above; the
+    gradient per tet is bounded by C rtol max|grad|."""
+    case = chamber_case(16, 15)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    P = lib.Problem(M, eps, FREQ, n_sub=8, precision=precision, rtol=rtol, max_iter=400, sweep_engine=engine)
+    S = P.forward_solve(tx, rx)
+    ref, S_meas, J_o, grad_o, extra = _oracle_reference("chamber", mesh, topo, eps, tx, rx)
+    S_o = ref["S"]
+    db, rel = _db_bins(S, S_o)
+    assert db.min() < -60.0, db.min()  # the case spans the three bins
+    C = 1e3
+    report = {}
+    for hi, lo in ((0.0, -20.0), (-20.0, -60.0), (-60.0, float(db.min()))):
+        sel = (db <= hi) & (db >= lo)
+        assert sel.any()
+        report[f"{hi:g}..{lo:.0f} dB"] = float(rel[sel].max())
+        assert rel[sel].max() <= C * rtol * 10.0 ** (-lo / 20.0), report
+    J, grad = P.misfit_and_gradient(S_meas)
+    assert np.abs(grad - grad_o).max() <= C * rtol * np.abs(grad_o).max()
+    P.close()
