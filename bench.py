@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--clocks-csv", default=None, help="directory for the nvidia-smi clock samples (CSV)")
     ap.add_argument("--serve", type=int, default=0,
                     help="run the serving scenario with this many Poisson requests instead of the gradient step")
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="requests of the serving scenario measured after the gradient step (0: skip)")
     ap.add_argument("--serve-freq-step", type=float, default=10e6,
                     help="frequency grid of the serving requests (Hz) in 0.8-1.2 GHz")
     ap.add_argument("--recycle-steps", type=int, default=3,
@@ -521,8 +523,16 @@ def cpu_oracle_sample(ctx):
         h = np.vdot(x, y)
         y = y - h * x
     t_gs = (time.perf_counter() - t0) / 10
+    # the main process's share of one pooled apply: the input copied into
+    # shared memory and the workers' partial results summed
+    parts = np.zeros((ctx["cores"], n), dtype=np.complex128)
+    t0 = time.perf_counter()
+    z = x.copy()
+    for w in range(1, ctx["cores"]):
+        z += parts[w]
+    t_comb = time.perf_counter() - t0
     per_worker = ctx["nsub"] / ctx["cores"]            # subdomains per process in a full pool
-    t_apply = per_worker * t_solve
+    t_apply = per_worker * t_solve + t_comb
     it = ORACLE_ITERATIONS
     t_col = it * (t_apply + t_spmm) + t_spmm + 0.5 * it * (it + 1) * t_gs
     t_fact = per_worker * float(np.mean(ctx["t_factor"]))
@@ -560,72 +570,101 @@ def cpu_baseline(args):
             "s_per_step": round(smp["step"], 1)}
 
 
-def run_serving(args):
-    """Serving scenario: Poisson arrivals of imaging requests on three resident
-    chamber meshes (about 50k tets at order 2, 200k and 500k tets at order 1),
-    32-160 transmitters in rings of 32, frequencies on a 10 MHz grid of
-    0.8-1.2 GHz, forward or misfit+gradient, problems cached per (mesh,
-    frequency) under a 150 GB budget; arrival rate set to 70 % of the capacity
-    measured on a calibration sample.  One JSON line."""
+def serving_setup(specs):
+    """Meshes of the serving scenario and the request executor: a forward batch
+    solves the columns of all its requests at once and hands every request the
+    S block of its own antennas; a gradient request adds the adjoint solve and
+    the gradient against measurements made from its forward S with 5 % seeded
+    noise.  Every problem gets its own CUDA stream."""
     import torch
 
     from paper_1607_02573_gb300 import mwi
-    from paper_1607_02573_gb300 import serve as SV
     from synthetic import antenna_array, chamber_eps, chamber_mesh, ring_antennas
-
-    torch.cuda.set_device(0)
-    specs = {"chamber50k_o2": (23, 21, 2, 16), "chamber200k_o1": (36, 34, 1, 64), "chamber500k_o1": (48, 45, 1, 64)}
     meshes = {}
     for name, (nxy, nz, order, nsub) in specs.items():
         m = chamber_mesh(nxy, nz)
         meshes[name] = (mwi.Mesh(m.xyz, m.tet, m.bface_tag, order=order), chamber_eps(m.xyz, m.tet), nsub, m.nt)
     rings = [antenna_array(ring_antennas(32, z=z)) for z in (0.06, 0.10, 0.14, 0.18, 0.22)]
+    opts = dict(precision=1, rtol=RTOL, max_iter=500, max_block=32)
 
     def make(key):
         M, eps, nsub, _ = meshes[key[0]]
-        return mwi.Problem(M, eps, key[1], n_sub=nsub, precision=1, rtol=RTOL, max_iter=500, max_block=32)
+        return mwi.Problem(M, eps, key[1], stream=torch.cuda.Stream(), n_sub=nsub, **opts)
 
-    def run(P, r):
-        k = r.n_rhs // 32
-        ants = np.concatenate([rings[(i + r.seed) % 5] for i in range(k)])
-        S = P.forward_solve(ants, ants)
-        if r.kind == "forward":
-            return r.n_rhs
+    def estimate(key):
+        M, _, nsub, _ = meshes[key[0]]
+        return M.estimate_bytes(160, n_sub=nsub, **opts)
+
+    def ants_of(r):
+        return np.concatenate([rings[(i + r.seed) % 5] for i in range(r.n_rhs // 32)])
+
+    def run_batch(P, batch):
+        out = {}
+        if batch[0].kind == "forward":
+            sets = [ants_of(r) for r in batch]
+            tx = np.concatenate(sets)
+            S = P.forward_solve(tx, tx)
+            off = 0
+            for r, a in zip(batch, sets):
+                out[r.rid] = (r.n_rhs, S[off:off + len(a), off:off + len(a)].copy())
+                off += len(a)
+            return out
+        r = batch[0]
+        tx = ants_of(r)
+        S = P.forward_solve(tx, tx)
         rng = np.random.default_rng(r.seed)
         noise = rng.standard_normal(S.shape) + 1j * rng.standard_normal(S.shape)
-        P.misfit_and_gradient(S * (1 + 0.05 * noise / np.sqrt(2)))
-        return 2 * r.n_rhs
+        J, grad = P.misfit_and_gradient(S * (1 + 0.05 * noise / np.sqrt(2)))
+        out[r.rid] = (2 * r.n_rhs, (S, J, grad))
+        return out
 
+    return meshes, make, estimate, run_batch
+
+
+def run_serving(args, n_requests=None):
+    """Serving scenario: Poisson arrivals in real time of imaging requests on
+    three resident chamber meshes (about 50k tets at order 2, 200k and 500k
+    tets at order 1), 32-160 transmitters in rings of 32, frequencies on a
+    10 MHz grid of 0.8-1.2 GHz, forward or misfit+gradient; continuous
+    batching over 3 slots (own streams), forward requests of one problem
+    merged up to 160 columns, problems cached per (mesh, frequency) under a
+    150 GB budget.  The arrival rate is 80 % of the sequential capacity
+    measured on a calibration sample.  Returns the summary dict."""
+    import torch
+
+    from paper_1607_02573_gb300 import serve as SV
+
+    torch.cuda.set_device(0)
+    n_requests = n_requests or args.serve
+    specs = {"chamber50k_o2": (23, 21, 2, 16), "chamber200k_o1": (36, 34, 1, 64), "chamber500k_o1": (48, 45, 1, 64)}
+    meshes, make, estimate, run_batch = serving_setup(specs)
     budget = 150 * 10 ** 9
     names = list(specs)
-    # calibration: median service time of a sample of requests (its own cache,
-    # freed afterwards; the median leaves out each mesh's one-time
-    # decomposition); the measured run arrives at 70 % of that capacity
     step = args.serve_freq_step
-    cal = SV.make_requests(max(6, args.serve // 5), rate=1.0, meshes=names, seed=98, freq_step=step)
-    cache = SV.ProblemCache(budget, make, SV.device_bytes, lambda P: P.close())
-    cal_recs, _ = SV.serve(cal, cache, run)
+    close = lambda P: P.close()  # noqa: E731
+    # calibration: sequential service time of a sample (one slot, no merging)
+    cal = SV.make_requests(max(8, n_requests // 6), rate=1e6, meshes=names, seed=98, freq_step=step)
+    cache = SV.ProblemCache(budget, make, SV.device_bytes, close, estimate=estimate)
+    srv = SV.Server(cache, run_batch, slots=1, merge=False)
+    SV.replay(cal, srv)
+    service = [x["service"] for x in srv.records.values() if x["status"] == "done"]
     cache.clear()
-    rate = 0.7 / float(np.median([x["service"] for x in cal_recs]))
-    reqs = SV.make_requests(args.serve, rate=rate, meshes=names, seed=99, freq_step=step)
-    cache = SV.ProblemCache(budget, make, SV.device_bytes, lambda P: P.close())
-    recs, summ = SV.serve(reqs, cache, run)
+    rate = 0.8 / float(np.median(service))
+    reqs = SV.make_requests(n_requests, rate=rate, meshes=names, seed=99, freq_step=step)
+    cache = SV.ProblemCache(budget, make, SV.device_bytes, close, estimate=estimate)
+    srv = SV.Server(cache, run_batch, slots=3, merge=True, max_cols=160)
+    summ = SV.replay(reqs, srv)
     peak = max(cache.seen.values()) if cache.seen else 0
     cache.clear()
     for M, _, _, _ in meshes.values():
         M.close()
-    line = {"metric": "serving: latency and RHS-solves/s under Poisson arrivals", "unit": UNIT,
-            "value": round(summ["rhs_solves_per_s"], 3), "higher_is_better": True, "n_gpus": 1,
-            "latency_p50_s": round(summ["latency_p50_s"], 4), "latency_p99_s": round(summ["latency_p99_s"], 4),
-            "requests": summ["requests"], "columns": summ["columns"], "arrival_rate_per_s": round(rate, 3),
-            "busy_fraction": round(summ["busy_fraction"], 3), "cache_hits": summ["cache_hits"],
-            "cache_misses": summ["cache_misses"], "evictions": summ["evictions"],
-            "largest_problem_bytes": int(peak), "budget_bytes": budget,
-            "meshes": {k: {"tets": v[3], "order": specs[k][2], "n_sub": specs[k][3]} for k, v in meshes.items()},
-            "service_s_p50": round(float(np.percentile([x["service"] for x in recs], 50)), 4),
-            "service_s_p99": round(float(np.percentile([x["service"] for x in recs], 99)), 4),
-            "freq_step_hz": step, "data": "synthetic", "dtype": "c64+df64", "rtol": RTOL}
-    print(json.dumps(line))
+    done = [x for x in srv.records.values() if x["status"] == "done"]
+    return dict(summ, arrival_rate_per_s=round(rate, 3), largest_problem_bytes=int(peak), budget_bytes=budget,
+                service_s_p50=float(np.percentile([x["service"] for x in done], 50)),
+                service_s_p99=float(np.percentile([x["service"] for x in done], 99)),
+                calibration_service_s_median=float(np.median(service)),
+                meshes={k: {"tets": v[3], "order": specs[k][2], "n_sub": specs[k][3]} for k, v in meshes.items()},
+                freq_step_hz=step, slots=3, max_cols=160, rtol=RTOL)
 
 
 def run_solve(args):
@@ -727,7 +766,10 @@ def main():
 
     if args.serve > 0:
         if rank == 0:
-            run_serving(args)
+            summ = run_serving(args)
+            print(json.dumps({"metric": "serving: latency and RHS-solves/s under Poisson arrivals", "unit": UNIT,
+                              "value": round(summ["rhs_solves_per_s"], 3), "higher_is_better": True, "n_gpus": 1,
+                              "data": "synthetic", "dtype": "c64+df64", **summ}))
         return
     if args.solve:
         if rank == 0:
@@ -834,6 +876,12 @@ def main():
                                 "fwd": f["fwd_info"], "adj": f["adj_info"]}
     if R.get("errors"):
         line["errors"] = R["errors"]
+    if args.serve_requests > 0 and not args.only_mixed and world == 1:
+        summ = run_serving(args, args.serve_requests)
+        line["serving"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
+        line["serving"]["what"] = ("Poisson arrivals in real time, latency from arrival to results on the host; "
+                                   "continuous batching over 3 slots with own streams, forward requests of one "
+                                   "problem merged, problem cache under a 150 GB budget")
     if cpu_line:
         line["cpu_baseline"] = cpu_line
     print(json.dumps(line))

@@ -334,6 +334,17 @@ mwi_status mwi_oras_traffic(mwi_problem_t prob, int32_t m, double* bytes);
  * counted.  For admission against a memory budget (a serving cache). */
 mwi_status mwi_problem_device_bytes(mwi_problem_t prob, int64_t* bytes);
 
+/* Upper estimate of the device bytes a problem on this mesh with these
+ * options will hold after solves of n_rhs transmitters (its operator,
+ * factors, field blocks and solver workspaces, as mwi_problem_device_bytes
+ * counts them), computed on the host before the problem exists: builds (or
+ * reuses) the mesh's decomposition and symbolic factorisation, which the
+ * problem would build anyway, and allocates only the mesh's shared operator
+ * structure.  For admission against a memory budget before building a
+ * problem on a mesh not seen yet (no counterpart in the paper). */
+mwi_status mwi_problem_estimate_bytes(mwi_mesh_t mesh, const mwi_solver_opts* opts, int32_t n_rhs,
+                                      int64_t* bytes);
+
 /* Per-kernel timing since the last reset, from CUDA events recorded on the
  * problem's stream around every call (no synchronisation in between):
  * ms[0] SpMM, ms[1] ORAS apply, ms[2] orthogonalisation (CGS2 + norms),

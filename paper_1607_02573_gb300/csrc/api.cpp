@@ -1558,6 +1558,43 @@ mwi_status mwi_oras_traffic(mwi_problem_t P, int32_t m, double* bytes) {
     });
 }
 
+mwi_status mwi_problem_estimate_bytes(mwi_mesh_t M, const mwi_solver_opts* opts, int32_t n_rhs, int64_t* bytes) {
+    return guard([&] {
+        MWI_REQUIRE(M && bytes && n_rhs >= 1, MWI_EINVAL, "bad argument");
+        const mwi_solver_opts o = defaults(opts);
+        MWI_REQUIRE(o.precision >= 0 && o.precision <= 2, MWI_EINVAL, "precision must be 0, 1 or 2");
+        std::shared_ptr<DecompEntry> E;
+        {
+            std::lock_guard<std::mutex> lk(M->mu);
+            ensure_global(M);
+            E = get_decomp(M, o);
+        }
+        const FrontsDev& F = E->F;
+        const double n = (double)M->T.ndof, nt = (double)M->T.nt, nnz = (double)M->A.nnz;
+        const double m = std::min(n_rhs, o.max_block), mall = n_rhs;
+        const bool mixed = o.precision != 0, nested = o.precision == 2;
+        const double fe = mixed ? 8.0 : 16.0;  // bytes of a factor entry
+        const double r = o.restart;
+        double b = nt * 16 + (double)M->A_fu.face.size() * 16 + nnz * 16 + (double)E->D.B_faces.face.size() * 16 +
+                   (double)E->B.nnz * 16;
+        b += nested ? nnz * 8 : (mixed ? 2 * nnz * 8 : 0);
+        b += ((double)F.ws_total() + (double)F.inv_entries + (double)F.sch_entries[0] + (double)F.sch_entries[1]) * fe;
+        if (mixed && o.sweep_engine == 4) b += 2.0 * (double)F.tiled_floats * 4;
+        // fields of every column (forward, adjoint, right-hand sides), block copies, residual
+        b += 3 * n * mall * 16 + 3 * n * m * 16;
+        // local and update vectors of the ORAS application
+        b += (2 * (double)F.nloc + (double)F.upd_rows) * m * fe + 2 * n * m * 8;
+        if (o.block_krylov) b += (r + 2) * n * m * 16 + 2 * n * m * 16;
+        else if (o.precision == 1) b += ((r + 1) * 2 + r + 2) * n * m * 8 + 3 * 2 * n * m * 8;
+        else if (nested) b += (13 + 12 + 1) * n * m * 16 + (o.inner_iters * 2 + 2) * n * m * 8;
+        else b += (2 * r + 2) * n * m * 16;
+        if (o.recycle) b += 64 * n * (16 + 8 + 8) + 2 * 64 * n * 8 + n * m * 16;
+        // small per-column and reduction arrays
+        b += (double)kDotBlocks * (2 * r + 3) * m * 16 + 64.0 * r * r * m + nt * 16;
+        *bytes = (int64_t)(1.1 * b) + ((int64_t)16 << 20);
+    });
+}
+
 mwi_status mwi_problem_device_bytes(mwi_problem_t P, int64_t* bytes) {
     return guard([&] {
         MWI_REQUIRE(P && bytes, MWI_EINVAL, "null argument");

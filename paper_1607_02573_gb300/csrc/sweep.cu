@@ -520,16 +520,19 @@ template <typename C>
 void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, const SweepCfg& sc,
                         cudaStream_t st) {
     const int nlev = (int)F.level_ptr.size() - 1;
-    const bool tc5 = sc.tc == 4;
+    // the tcgen05 engine moves right-hand-side rows by 16-byte bulk copies:
+    // an odd column count takes the mma.sync TF32 engine
+    const bool tc5 = sc.tc == 4 && (m % 2) == 0;
+    const int tc = sc.tc == 4 ? 2 : sc.tc;
     MWI_REQUIRE(!tc5 || (sc.wt && sc.err), MWI_EINVAL, "internal: tensor-core sweeps without the tiled panels");
     for (int l = 0; l < nlev; ++l) {
         launch_gather<C>(F, l, Y, upd, m, st);
         if (tc5) launch_tc_product<C>(F, l, false, ws, Y, Z, upd, m, sc, st);
-        else launch_gemm<C, kFwd>(F, l, ws, Y, Z, upd, m, sc.tc, st);
+        else launch_gemm<C, kFwd>(F, l, ws, Y, Z, upd, m, tc, st);
     }
     for (int l = nlev - 1; l >= 0; --l) {
         if (tc5) launch_tc_product<C>(F, l, true, ws, Y, Z, upd, m, sc, st);
-        else launch_gemm<C, kBwd>(F, l, ws, Y, Z, upd, m, sc.tc, st);
+        else launch_gemm<C, kBwd>(F, l, ws, Y, Z, upd, m, tc, st);
     }
 }
 

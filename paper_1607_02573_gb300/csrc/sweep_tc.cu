@@ -33,14 +33,22 @@
 //
 // Kernel: persistent, one CTA per SM, tiles (front, 128-row tile, 32-column
 // chunk) taken in a fixed stride.  Warp roles:
-//   warp 0      one lane issues the panel bulk copies (mbarrier transaction count)
+//   warp 0      bulk copies: lane 0 the panel blocks, every lane one
+//               right-hand-side row (256 B) into the stage's staging rows
+//               (the update-row indices of the backward product looked up
+//               by the lanes first), one mbarrier transaction count
 //   warp 1      owns the tensor memory (2 x 128 columns: accumulators double
 //               buffered across tiles); one lane issues tcgen05.mma and commits
-//   warps 2-5   gather the right-hand-side rows into the swizzled B stage
+//   warps 2-5   transpose the staging rows into the K-major B tile (shared
+//               memory only)
 //   warps 6-9   epilogue: tcgen05.ld, complex combine, D^{-1} scaling or
 //               extend-add of the children's update rows, global stores
-// Stages (4 x 40 KB) form a ring shared by all tiles of the CTA, so loads of
-// the next tile overlap the products and the epilogue of the current one.
+// Stages (4 x 48 KB) form a ring shared by all tiles of the CTA, so loads of
+// the next tile overlap the products and the epilogue of the current one; no
+// thread waits on device memory inside a stage except the copy lanes' index
+// lookups.  The right-hand-side rows move by 16-byte-aligned bulk copies, so
+// the engine needs an even number of columns (the solver falls back to the
+// mma.sync engine otherwise).
 // Every wait is bounded: on expiry the kernel records an error code, the
 // other roles stop at their next wait, and the CTA frees its tensor memory
 // and returns.
@@ -56,10 +64,11 @@ constexpr int kStages = 4;
 constexpr int kKS = 4;                      // K chunks of 8 per stage (K = 32)
 constexpr int kAStage = 32768;              // 4 K chunks x 16 groups of 8 M lines x 2 planes x 256 B
 constexpr int kBStage = 8192;               // 64 real columns x 32 K floats
-constexpr int kStage = kAStage + kBStage;
+constexpr int kStage = kAStage + 2 * kBStage;  // + the staging rows [32][32 complex] of the copies
 constexpr int kThreads = 320;
 constexpr int kTmemCols = 256;
 constexpr int kSmemBytes = kStages * kStage + 1024 /* barriers */ + 1024 /* alignment */;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
 constexpr long long kWaitLimit = 1ll << 24;
 
 enum { kFwdT = 0, kBwdT = 1 };
@@ -90,9 +99,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
                                           int code) {
     for (long long it = 0; it < kWaitLimit; ++it) {
-        if (mbar_try(bar, parity)) return true;
+        if (mbar_try(bar, parity)) return true;  // try_wait suspends in hardware for a while
         if (*abort_flag) return false;
-        if (it > 32) __nanosleep(64);
+        if (it > (1 << 20)) __nanosleep(256);
     }
     *abort_flag = 1;
     atomicExch(err, code);
@@ -190,6 +199,13 @@ __device__ __forceinline__ TcGeom tc_geom(const TileDesc& d) {
     return g;
 }
 
+// number of the stage's 32 K rows that hold data (the rest of the B tile is zero)
+template <int MODE>
+__device__ __forceinline__ int stage_rows(const TcGeom& G, int st) {
+    const int lim = MODE == kFwdT ? min(G.p, G.row0 + 128) - st * 32 : G.f - (G.row0 + st * 32);
+    return max(0, min(32, lim));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
     const TileDesc* __restrict__ tiles, int ntiles, int nchunks, const int32_t* __restrict__ urows,
@@ -199,24 +215,27 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~(uintptr_t)1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStage);
-    // bars: full[kStages], empty[kStages], tfull[2], tempty[2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+    // bars: raw[kStages] (copies landed), full[kStages] (B tile ready), empty[kStages]
+    // (stage consumed), tfull[2], tempty[2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbase = smem_u32(smem);
-    auto full_bar = [&](int s) { return smem_u32(bars + s); };
-    auto empty_bar = [&](int s) { return smem_u32(bars + kStages + s); };
-    auto tfull_bar = [&](int b) { return smem_u32(bars + 2 * kStages + b); };
-    auto tempty_bar = [&](int b) { return smem_u32(bars + 2 * kStages + 2 + b); };
+    auto raw_bar = [&](int s) { return smem_u32(bars + s); };
+    auto full_bar = [&](int s) { return smem_u32(bars + kStages + s); };
+    auto empty_bar = [&](int s) { return smem_u32(bars + 2 * kStages + s); };
+    auto tfull_bar = [&](int b) { return smem_u32(bars + 3 * kStages + b); };
+    auto tempty_bar = [&](int b) { return smem_u32(bars + 3 * kStages + 2 + b); };
 
-    // stale shared memory must be finite: the MMA reads whole atoms, and the
+    // stale shared memory must be finite: the MMA reads whole blocks, and the
     // zero right-hand-side rows only cancel finite factor entries
     for (int i = threadIdx.x; i < kStages * kStage / 16; i += kThreads)
         reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
     fence_proxy_async();
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(full_bar(s), 1 + 4);  // the copy lane (with its transaction bytes) + 4 gather warps
+            mbar_init(raw_bar(s), 1);       // the copy lane, with the stage's transaction bytes
+            mbar_init(full_bar(s), 4);      // the 4 transpose warps
             mbar_init(empty_bar(s), 1);     // tcgen05.commit
         }
         for (int b = 0; b < 2; ++b) {
@@ -238,26 +257,43 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
     const int total = ntiles * nchunks;
 
     if (warp == 0) {
-        // ---------------- panel copies
-        if (lane == 0) {
-            long long g = 0;
-            bool ok = true;
-            for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x) {
-                const TileDesc d = tiles[ti / nchunks];
-                const TcGeom G = tc_geom<MODE>(d);
-                const float* P = wt + d.a_off;
-                for (int st = 0; st < G.nst && ok; ++st, ++g) {
-                    const int s = (int)(g % kStages);
-                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                    if (!(ok = mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 1))) break;
-                    const uint32_t a_dst = sbase + s * kStage;
-                    const int c0 = G.k0 + st * kKS, nc = min(kKS, G.k0 + G.nk - c0);
-                    const uint32_t bytes = (uint32_t)G.ng * 512u;
-                    mbar_arrive_tx(full_bar(s), bytes * nc);
-                    for (int c = 0; c < nc; ++c)
-                        bulk_g2s(a_dst + c * 8192, P + ((int64_t)(c0 + c) * G.cstride + G.g0) * 128, bytes,
-                                 full_bar(s));
+        // ---------------- bulk copies: panel blocks (lane 0) and one
+        // right-hand-side row per lane into the stage's staging rows
+        long long g = 0;
+        bool ok = true;
+        for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x) {
+            const TileDesc d = tiles[ti / nchunks];
+            const TcGeom G = tc_geom<MODE>(d);
+            const int c0 = (ti % nchunks) * 32, nc = min(32, m - c0);
+            const uint32_t row_bytes = (uint32_t)nc * 8u;
+            const float* P = wt + d.a_off;
+            const int32_t* ur = urows + d.u_off;
+            for (int st = 0; st < G.nst; ++st, ++g) {
+                const int s = (int)(g % kStages);
+                const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                // the source row of this lane, looked up before the stage is free
+                const int nv = stage_rows<MODE>(G, st);
+                const float2* src = nullptr;
+                if (lane < nv) {
+                    if (MODE == kFwdT) {
+                        src = Y + (d.rowbase + st * 32 + lane) * m + c0;
+                    } else {
+                        const int i = G.row0 + st * 32 + lane;
+                        src = i < G.p ? Z + (d.rowbase + i) * m + c0 : Y + (d.sbase + ur[i - G.p]) * m + c0;
+                    }
                 }
+                if (lane == 0) ok = mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 1);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                const uint32_t a_dst = sbase + s * kStage;
+                const int k0 = G.k0 + st * kKS, nk = min(kKS, G.k0 + G.nk - k0);
+                const uint32_t a_bytes = (uint32_t)G.ng * 512u;
+                if (lane == 0) mbar_arrive_tx(raw_bar(s), a_bytes * nk + row_bytes * nv);
+                __syncwarp();
+                if (lane < nk)
+                    bulk_g2s(a_dst + lane * 8192, P + ((int64_t)(k0 + lane) * G.cstride + G.g0) * 128, a_bytes,
+                             raw_bar(s));
+                if (lane < nv) bulk_g2s(a_dst + kAStage + kBStage + lane * 256, src, row_bytes, raw_bar(s));
             }
         }
     } else if (warp == 1) {
@@ -280,8 +316,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                     if (!(ok = mbar_wait(full_bar(s), ph, abort_flag, err, 3))) break;
                     tc_fence_after();
                     const uint32_t a0 = sbase + s * kStage, b0 = a0 + kAStage;
-                    const int nc = min(kKS, G.nk - st * kKS);
-                    for (int c = 0; c < nc; ++c) {
+                    const int nk = min(kKS, G.nk - st * kKS);
+                    for (int c = 0; c < nk; ++c) {
                         // B: 64 lines (real columns) of 128 B, K step c = bytes 32c of every line
                         const uint64_t bd = smem_desc(b0 + c * 32, 1024, kSw128);
                         const uint32_t acc = (st > 0 || c > 0) ? 1u : 0u;
@@ -295,48 +331,38 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
             }
         }
     } else if (warp < 6) {
-        // ---------------- right-hand-side rows into the B stage
-        const int pw = warp - 2;
+        // ---------------- staging rows [32][32 complex] -> K-major B tile
+        // (line = real column, 32 K floats, 128-byte swizzle); thread: column
+        // `lane`, two groups of 4 rows
+        const int rg = warp - 2;
         long long g = 0;
         bool ok = true;
         for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x) {
             const TileDesc d = tiles[ti / nchunks];
             const TcGeom G = tc_geom<MODE>(d);
-            const int c = (ti % nchunks) * 32 + lane;
-            const bool cin = c < m;
-            const int32_t* ur = urows + d.u_off;
+            const bool cin = (ti % nchunks) * 32 + lane < m;
             for (int st = 0; st < G.nst; ++st, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                if (!(ok = mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 4))) break;
-                float2 v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int r = pw * 8 + j;  // K index within the stage
-                    const int k = G.row0 * (MODE == kBwdT) + st * kKS * 8 + r;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (cin) {
-                        if (MODE == kFwdT) {
-                            if (k < min(G.p, G.row0 + 128)) x = Y[(d.rowbase + k) * m + c];
-                        } else {
-                            if (k < G.p) x = Z[(d.rowbase + k) * m + c];
-                            else if (k < G.f) x = Y[(d.sbase + ur[k - G.p]) * m + c];
-                        }
-                    }
-                    v[j] = x;
-                }
-                // line n = 2 lane (re) and 2 lane + 1 (im), 128-byte swizzled position of K index r
+                if (!(ok = mbar_wait(raw_bar(s), ph, abort_flag, err, 4))) break;
+                const int nv = stage_rows<MODE>(G, st);
                 unsigned char* B = smem + s * kStage + kAStage;
+                const float2* R = reinterpret_cast<const float2*>(B + kBStage);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int r = pw * 8 + j;
+                for (int h = 0; h < 2; ++h) {
+                    const int q = rg * 2 + h;  // rows 4q .. 4q+3
+                    float2 v[4];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int n = 2 * lane + h;
-                        *reinterpret_cast<float*>(B + (n >> 3) * 1024 + (n & 7) * 128 +
-                                                  ((((r >> 2) ^ (n & 7)) << 4) | ((r & 3) << 2))) =
-                            h ? v[j].y : v[j].x;
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = 4 * q + j;
+                        v[j] = (cin && r < nv) ? R[r * 32 + lane] : make_float2(0.f, 0.f);
                     }
+                    const int n0 = 2 * lane;
+                    *reinterpret_cast<float4*>(B + (n0 >> 3) * 1024 + (n0 & 7) * 128 + ((q ^ (n0 & 7)) << 4)) =
+                        make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+                    const int n1 = n0 + 1;
+                    *reinterpret_cast<float4*>(B + (n1 >> 3) * 1024 + (n1 & 7) * 128 + ((q ^ (n1 & 7)) << 4)) =
+                        make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
                 }
                 fence_proxy_async();
                 __syncwarp();
@@ -388,18 +414,36 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                 dst = Z + (d.rowbase + gi) * m + c0;
             } else if (gi < d.f) {
                 const int2 src = asm2[d.asm_base + gi];
+                if (nc == 32 && (m & 1) == 0) {
+                    // the children's rows, 16 bytes at a time
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    if (q < nc) {
-                        if (src.x >= 0) {
-                            const float2 a = upd[(int64_t)src.x * m + c0 + q];
-                            o[2 * q] += a.x;
-                            o[2 * q + 1] += a.y;
+                    for (int h = 0; h < 2; ++h) {
+                        const int sr = h ? src.y : src.x;
+                        if (sr < 0) continue;
+                        const float4* a = reinterpret_cast<const float4*>(upd + (int64_t)sr * m + c0);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const float4 v = a[q];
+                            o[4 * q] += v.x;
+                            o[4 * q + 1] += v.y;
+                            o[4 * q + 2] += v.z;
+                            o[4 * q + 3] += v.w;
                         }
-                        if (src.y >= 0) {
-                            const float2 a = upd[(int64_t)src.y * m + c0 + q];
-                            o[2 * q] += a.x;
-                            o[2 * q + 1] += a.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        if (q < nc) {
+                            if (src.x >= 0) {
+                                const float2 a = upd[(int64_t)src.x * m + c0 + q];
+                                o[2 * q] += a.x;
+                                o[2 * q + 1] += a.y;
+                            }
+                            if (src.y >= 0) {
+                                const float2 a = upd[(int64_t)src.y * m + c0 + q];
+                                o[2 * q] += a.x;
+                                o[2 * q + 1] += a.y;
+                            }
                         }
                     }
                 }

@@ -78,6 +78,7 @@ _SIGS = {
     "mwi_decomposition": [_vp, _i32p, _i64p],
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
     "mwi_problem_device_bytes": [_vp, _i64p],
+    "mwi_problem_estimate_bytes": [_vp, C.POINTER(mwi_solver_opts), C.c_int32, _i64p],
     "mwi_oras_traffic": [_vp, C.c_int32, _dp],
     "mwi_update_kappa_device": [_vp, _vp],
     "mwi_misfit_and_gradient_kappa_device": [_vp, _vp, _vp, C.c_double, _dp, _dp, _vp, C.POINTER(mwi_solve_info)],
@@ -164,6 +165,13 @@ class Mesh:
         n = C.c_int64()
         check(mwi_mesh_ndof(h, C.byref(n)))
         self.ndof = n.value
+
+    def estimate_bytes(self, n_rhs, **opts):
+        """Upper estimate of the device bytes of a problem on this mesh (mwi_problem_estimate_bytes)."""
+        o, keep = make_opts(**opts)
+        b = C.c_int64()
+        check(mwi_problem_estimate_bytes(self.h, C.byref(o), int(n_rhs), C.byref(b)))
+        return b.value
 
     def dof_keys(self):
         kind = np.empty(self.ndof, dtype=np.int32)

@@ -85,13 +85,16 @@ def test_partition_matches_oracle_rcb(lib):
     P.close()
 
 
+@pytest.mark.parametrize("m", [3, 6, 40])
 @pytest.mark.parametrize("precision,engine,tol", [(0, 0, 1e-10), (1, 1, 2e-5), (1, 3, 2e-5), (1, 2, 5e-3),
                                                   (1, 4, 1e-2)])
-def test_oras_apply_parity(lib, precision, engine, tol):
+def test_oras_apply_parity(lib, precision, engine, tol, m):
     """engine: complex FP32 sweeps on tensor cores with split TF32 operands (1),
     plain TF32 (2, about 1e-3 relative), CUDA cores (3), or tcgen05 TF32 with
     bulk-copied tiled panels (4: the tensor core truncates the FP32 operands
-    to TF32, up to 2^-10 relative per operand)."""
+    to TF32, up to 2^-10 relative per operand; an odd column count falls back
+    to engine 2).  m: columns -- odd, even, and two 32-column chunks with a
+    ragged second one."""
     case = chamber_case(12, 11)
     mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
     part = dd.rcb_partition(mesh.xyz, mesh.tet, 6)
@@ -99,7 +102,6 @@ def test_oras_apply_parity(lib, precision, engine, tol):
     dec = dd.Decomposition(mesh.xyz, mesh.tet, topo, part, 1)
     oras = dd.ORAS(dec, dd.local_matrices(mesh.xyz, topo, dec, eps, FREQ))
     rng = np.random.default_rng(1)
-    m = 3
     X = rng.standard_normal((M.ndof, m)) + 1j * rng.standard_normal((M.ndof, m))
     Y = P.oras_apply(torch.from_numpy(X).cuda()).cpu().numpy()
     inv = np.argsort(perm)
