@@ -31,7 +31,7 @@
 // low 13 mantissa bits -- FP32 accumulation); then
 //   Re C(i, c) = Dr[i][2c] - Di[i][2c+1],  Im C(i, c) = Dr[i][2c+1] + Di[i][2c].
 //
-// Kernel: persistent, one CTA per SM, tiles (front, 128-row tile, 32-column
+// Kernel: persistent, two CTAs per SM, tiles (front, 128-row tile, 32-column
 // chunk) taken in a fixed stride.  Warp roles:
 //   warp 0      bulk copies: lane 0 the panel blocks, every lane one
 //               right-hand-side row (256 B) into the stage's staging rows
@@ -39,12 +39,13 @@
 //               by the lanes first), one mbarrier transaction count
 //   warp 1      owns the tensor memory (2 x 128 columns: accumulators double
 //               buffered across tiles); one lane issues tcgen05.mma and commits
-//   warps 2-5   transpose the staging rows into the K-major B tile (shared
+//   warps 2-3   transpose the staging rows into the K-major B tile (shared
 //               memory only)
-//   warps 6-9   epilogue: tcgen05.ld, complex combine, D^{-1} scaling or
+//   warps 4-7   epilogue: tcgen05.ld, complex combine, D^{-1} scaling or
 //               extend-add of the children's update rows, global stores
-// Stages (4 x 48 KB) form a ring shared by all tiles of the CTA, so loads of
-// the next tile overlap the products and the epilogue of the current one; no
+// Stages (2 x 48 KB per CTA, two CTAs per SM) form a ring shared by all tiles
+// of the CTA, so loads of the next tile overlap the products and the epilogue
+// of the current one; no
 // thread waits on device memory inside a stage except the copy lanes' index
 // lookups.  The right-hand-side rows move by 16-byte-aligned bulk copies, so
 // the engine needs an even number of columns (the solver falls back to the
@@ -60,15 +61,17 @@
 namespace mwi {
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 2;                  // stage ring per CTA (two CTAs per SM)
+constexpr int kCtasPerSm = 2;
+constexpr int kUrCache = 1024;              // update-row indices of a backward tile kept in shared memory
 constexpr int kKS = 4;                      // K chunks of 8 per stage (K = 32)
 constexpr int kAStage = 32768;              // 4 K chunks x 16 groups of 8 M lines x 2 planes x 256 B
 constexpr int kBStage = 8192;               // 64 real columns x 32 K floats
 constexpr int kStage = kAStage + 2 * kBStage;  // + the staging rows [32][32 complex] of the copies
-constexpr int kThreads = 320;
+constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;
-constexpr int kSmemBytes = kStages * kStage + 1024 /* barriers */ + 1024 /* alignment */;
-static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
+constexpr int kSmemBytes = kStages * kStage + 1024 /* barriers */ + kUrCache * 4 + 1024 /* alignment */;
+static_assert(kSmemBytes * kCtasPerSm <= 228 * 1024 - 2048, "shared memory per SM");
 constexpr long long kWaitLimit = 1ll << 24;
 
 enum { kFwdT = 0, kBwdT = 1 };
@@ -207,7 +210,7 @@ __device__ __forceinline__ int stage_rows(const TcGeom& G, int st) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) sweep_tc_kernel(
     const TileDesc* __restrict__ tiles, int ntiles, int nchunks, const int32_t* __restrict__ urows,
     const int2* __restrict__ asm2, const float* __restrict__ wt, const float2* __restrict__ dinv,
     float2* __restrict__ Y, float2* __restrict__ Z, float2* __restrict__ upd, int m, int* __restrict__ err) {
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
     // (stage consumed), tfull[2], tempty[2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int32_t* sur = reinterpret_cast<int32_t*>(smem + kStages * kStage + 1024);  // copy warp's index cache
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbase = smem_u32(smem);
     auto raw_bar = [&](int s) { return smem_u32(bars + s); };
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(raw_bar(s), 1);       // the copy lane, with the stage's transaction bytes
-            mbar_init(full_bar(s), 4);      // the 4 transpose warps
+            mbar_init(full_bar(s), 2);      // the 2 transpose warps
             mbar_init(empty_bar(s), 1);     // tcgen05.commit
         }
         for (int b = 0; b < 2; ++b) {
@@ -268,6 +272,15 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
             const uint32_t row_bytes = (uint32_t)nc * 8u;
             const float* P = wt + d.a_off;
             const int32_t* ur = urows + d.u_off;
+            // backward: the tile's update-row indices (at most kUrCache) into shared
+            // memory, one coalesced pass; the stages then look them up there
+            const int u = G.f - G.p;
+            const bool ur_cached = MODE == kBwdT && u <= kUrCache;
+            __syncwarp();
+            if (ur_cached) {
+                for (int j = lane; j < u; j += 32) sur[j] = ur[j];
+                __syncwarp();
+            }
             for (int st = 0; st < G.nst; ++st, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
@@ -279,7 +292,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                         src = Y + (d.rowbase + st * 32 + lane) * m + c0;
                     } else {
                         const int i = G.row0 + st * 32 + lane;
-                        src = i < G.p ? Z + (d.rowbase + i) * m + c0 : Y + (d.sbase + ur[i - G.p]) * m + c0;
+                        src = i < G.p ? Z + (d.rowbase + i) * m + c0
+                                      : Y + (d.sbase + (ur_cached ? sur[i - G.p] : ur[i - G.p])) * m + c0;
                     }
                 }
                 if (lane == 0) ok = mbar_wait(empty_bar(s), ph ^ 1, abort_flag, err, 1);
@@ -330,10 +344,10 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                 mma_commit(tfull_bar(buf));
             }
         }
-    } else if (warp < 6) {
+    } else if (warp < 4) {
         // ---------------- staging rows [32][32 complex] -> K-major B tile
         // (line = real column, 32 K floats, 128-byte swizzle); thread: column
-        // `lane`, two groups of 4 rows
+        // `lane`, four groups of 4 rows
         const int rg = warp - 2;
         long long g = 0;
         bool ok = true;
@@ -349,8 +363,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
                 unsigned char* B = smem + s * kStage + kAStage;
                 const float2* R = reinterpret_cast<const float2*>(B + kBStage);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int q = rg * 2 + h;  // rows 4q .. 4q+3
+                for (int h = 0; h < 4; ++h) {
+                    const int q = rg * 4 + h;  // rows 4q .. 4q+3
                     float2 v[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -379,86 +393,93 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(
             const TileDesc d = tiles[ti / nchunks];
             const int c0 = (ti % nchunks) * 32;
             const int buf = it & 1;
+            // loads that do not depend on the product, issued before waiting for it
+            const int gi = d.row0 + i;
+            float2 dv = make_float2(0.f, 0.f);
+            int2 src = make_int2(-1, -1);
+            if (MODE == kFwdT) {
+                if (gi < d.p) dv = dinv[d.rowbase + gi];
+                else if (gi < d.f) src = asm2[d.asm_base + gi];
+            }
             if (!(ok = mbar_wait(tfull_bar(buf), (it >> 1) & 1, abort_flag, err, 5))) break;
             tc_fence_after();
-            float o[64];
             const uint32_t t0 = tmem + ((uint32_t)(lg * 32) << 16) + buf * 128;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float dr[32], di[32];
-                tmem_ld32(t0 + h * 32, dr);
-                tmem_ld32(t0 + 64 + h * 32, di);
-                tmem_ld_wait();
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    o[32 * h + 2 * q] = dr[2 * q] - di[2 * q + 1];
-                    o[32 * h + 2 * q + 1] = dr[2 * q + 1] + di[2 * q];
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty_bar(buf));
-            const int gi = d.row0 + i;
             const int nc = min(32, m - c0);
             float2* dst = nullptr;
             if (MODE == kBwdT) {
                 if (gi < d.p) dst = Y + (d.rowbase + gi) * m + c0;
             } else if (gi < d.p) {
-                const float2 dv = dinv[d.rowbase + gi];
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const float re = o[2 * q], im = o[2 * q + 1];
-                    o[2 * q] = re * dv.x - im * dv.y;
-                    o[2 * q + 1] = re * dv.y + im * dv.x;
-                }
                 dst = Z + (d.rowbase + gi) * m + c0;
             } else if (gi < d.f) {
-                const int2 src = asm2[d.asm_base + gi];
-                if (nc == 32 && (m & 1) == 0) {
-                    // the children's rows, 16 bytes at a time
+                dst = upd + (d.upd_row + gi - d.p) * m + c0;
+            }
+            const bool vec = nc == 32 && (m & 1) == 0;
+            // two halves of 16 complex columns: tensor-memory loads, combine,
+            // D^{-1} or the children's rows, stores; the accumulator is released
+            // once the second half is in registers
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int sr = h ? src.y : src.x;
-                        if (sr < 0) continue;
-                        const float4* a = reinterpret_cast<const float4*>(upd + (int64_t)sr * m + c0);
+            for (int h = 0; h < 2; ++h) {
+                float o[32];
+                {
+                    float dr[32], di[32];
+                    tmem_ld32(t0 + h * 32, dr);
+                    tmem_ld32(t0 + 64 + h * 32, di);
+                    tmem_ld_wait();
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const float4 v = a[q];
-                            o[4 * q] += v.x;
-                            o[4 * q + 1] += v.y;
-                            o[4 * q + 2] += v.z;
-                            o[4 * q + 3] += v.w;
-                        }
+                    for (int q = 0; q < 16; ++q) {
+                        o[2 * q] = dr[2 * q] - di[2 * q + 1];
+                        o[2 * q + 1] = dr[2 * q + 1] + di[2 * q];
                     }
-                } else {
+                }
+                if (h == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty_bar(buf));
+                }
+                if (!dst) continue;
+                const int cb = 16 * h;  // first complex column of the half
+                if (MODE == kFwdT && gi < d.p) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        if (q < nc) {
-                            if (src.x >= 0) {
-                                const float2 a = upd[(int64_t)src.x * m + c0 + q];
-                                o[2 * q] += a.x;
-                                o[2 * q + 1] += a.y;
+                    for (int q = 0; q < 16; ++q) {
+                        const float re = o[2 * q], im = o[2 * q + 1];
+                        o[2 * q] = re * dv.x - im * dv.y;
+                        o[2 * q + 1] = re * dv.y + im * dv.x;
+                    }
+                } else if (MODE == kFwdT) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int sr = k ? src.y : src.x;
+                        if (sr < 0) continue;
+                        const float2* a = upd + (int64_t)sr * m + c0 + cb;
+                        if (vec) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 v = reinterpret_cast<const float4*>(a)[q];
+                                o[4 * q] += v.x;
+                                o[4 * q + 1] += v.y;
+                                o[4 * q + 2] += v.z;
+                                o[4 * q + 3] += v.w;
                             }
-                            if (src.y >= 0) {
-                                const float2 a = upd[(int64_t)src.y * m + c0 + q];
-                                o[2 * q] += a.x;
-                                o[2 * q + 1] += a.y;
-                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                if (cb + q < nc) {
+                                    const float2 v = a[q];
+                                    o[2 * q] += v.x;
+                                    o[2 * q + 1] += v.y;
+                                }
                         }
                     }
                 }
-                dst = upd + (d.upd_row + gi - d.p) * m + c0;
-            }
-            if (dst) {
-                if (nc == 32 && (m & 1) == 0) {
+                if (vec) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        reinterpret_cast<float4*>(dst)[q] =
+                    for (int q = 0; q < 8; ++q)
+                        reinterpret_cast<float4*>(dst + cb)[q] =
                             make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        if (q < nc) dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
+                    for (int q = 0; q < 16; ++q)
+                        if (cb + q < nc) dst[cb + q] = make_float2(o[2 * q], o[2 * q + 1]);
                 }
             }
         }
@@ -525,7 +546,7 @@ int sweep_tc_ctas() {
         int dev = 0, sms = 0;
         MWI_CUDA(cudaGetDevice(&dev));
         MWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        n = std::max(1, sms);
+        n = std::max(1, sms * kCtasPerSm);
     }
     return n;
 }
