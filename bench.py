@@ -79,7 +79,8 @@ def parse():
                     help="skip the accuracy statement (mixed path against the FP64 path at rtol 1e-12)")
     ap.add_argument("--p1-steps", type=int, default=2,
                     help="timed gradient steps with the nodal (P1) parameter (0: skip)")
-    ap.add_argument("--engine", type=int, default=2, help="complex FP32 sweep engine (see mwi_solver_opts)")
+    ap.add_argument("--engine", type=int, default=0,
+                    help="complex FP32 sweep engine (see mwi_solver_opts; 0 = the library default, tcgen05)")
     ap.add_argument("--requests", type=int, default=200,
                     help="end-to-end gradient requests (host in, host out) for e2e throughput and p50/p99 latency")
     return ap.parse_args()
@@ -701,7 +702,7 @@ def run_solve(args):
             "oras_impl_bytes_per_call": P.oras_traffic(min(32, ants.shape[0])), "solve": info,
             "kernel_ms": dict(zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"],
                                   [round(v, 2) for v in kms.tolist()])),
-            "kernel_calls": kcnt.tolist(),
+            "kernel_calls": kcnt.tolist(), "levels": P.sweep_levels(),
             "reciprocity": float(np.linalg.norm(S - S.T) / np.linalg.norm(S))}
     P.close()
     M.close()

@@ -93,10 +93,14 @@ typedef struct {
     int32_t max_block;    /* right-hand sides per block solve; more transmitters are solved in
                              blocks of this width (Krylov memory grows with it) [64] */
     int32_t sweep_engine; /* MIXED modes, engine of the complex FP32 ORAS sweeps:
-                             0 = default (2); 1 = tensor cores, operands split into two TF32
-                             parts (about FP32 accuracy); 2 = tensor cores, plain TF32 (the
-                             preconditioner carries ~1e-3 relative rounding, absorbed by the
-                             outer FGMRES); 3 = CUDA cores, FP32 */
+                             0 = default (4); 1 = tensor cores (mma.sync), operands split into
+                             two TF32 parts (about FP32 accuracy); 2 = tensor cores (mma.sync),
+                             plain TF32; 3 = CUDA cores, FP32; 4 = fifth-generation tensor
+                             cores (tcgen05, TF32 operands, accumulators in tensor memory) fed
+                             by bulk copies from two tiled copies of the factor panels (about
+                             2.4 GB per GB of panels more device memory).  TF32 engines carry
+                             ~1e-3 relative rounding in the preconditioner, absorbed by the
+                             outer FGMRES */
     int32_t block_krylov; /* 0 = pseudo-block FGMRES: every column of a block keeps its own
                              Krylov space and the columns' operations are fused (Section 6.3)
                              [0]; 1 = true block FGMRES (the block methods of Section 7): one
@@ -333,6 +337,30 @@ mwi_status mwi_oras_traffic(mwi_problem_t prob, int32_t m, double* bytes);
  * the mesh and its decomposition, shared by the problems on that mesh, are not
  * counted.  For admission against a memory budget (a serving cache). */
 mwi_status mwi_problem_device_bytes(mwi_problem_t prob, int64_t* bytes);
+
+/* Per tree level of the multifrontal sweeps (deepest level first; a
+ * measurement aid, no counterpart in the paper): *n_levels levels; for the
+ * first max_levels of them the fronts, the partitioned-inverse panel entries
+ * (sum f p), the update rows (sum u), and the 128-row tiles of the forward
+ * (rows) and backward (pivots) tensor-core products.  Array arguments may be
+ * NULL. */
+mwi_status mwi_sweep_levels(mwi_problem_t prob, int32_t max_levels, int32_t* n_levels, int64_t* fronts,
+                            int64_t* panel_entries, int64_t* update_rows, int64_t* tiles_fwd,
+                            int64_t* tiles_bwd);
+
+/* Krylov recycling across problems (the recycling of Section 7, across the
+ * nearby frequencies of a multi-frequency measurement or of a serving cache):
+ * the resident forward solutions of src (and its adjoint solutions, if any)
+ * become the recycled space of dst, so that dst's next forward solve with the
+ * same transmitter count (at most 32) starts every column from the
+ * least-residual element of their span, and its next adjoint solve from the
+ * span of its own forward solutions and of src's adjoint solutions, exactly as
+ * after a solve of dst itself (see recycle in mwi_solver_opts).  Both problems
+ * must be on the same mesh; dst must have recycle = 1 (else MWI_ESTATE); src
+ * must hold forward solutions (else MWI_ESTATE).  Copies on dst's stream and
+ * returns when done; dst's previous fields are dropped.  The two handles must
+ * not be in use by other threads during the call. */
+mwi_status mwi_recycle_from(mwi_problem_t dst, mwi_problem_t src);
 
 /* Upper estimate of the device bytes a problem on this mesh with these
  * options will hold after solves of n_rhs transmitters (its operator,

@@ -223,7 +223,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     if (d.inner_rtol <= 0) d.inner_rtol = 1e-4;
     if (d.nd_leaf <= 0) d.nd_leaf = 64;
     if (d.max_block <= 0) d.max_block = 64;
-    if (d.sweep_engine <= 0) d.sweep_engine = 2;
+    if (d.sweep_engine <= 0) d.sweep_engine = 4;
     if (d.block_krylov < 0 || d.block_krylov > 1) throw Error(MWI_EINVAL, "block_krylov must be 0 or 1");
     if (d.recycle < 0 || d.recycle > 1) throw Error(MWI_EINVAL, "recycle must be 0 or 1");
     if (d.factor_reuse < 0) throw Error(MWI_EINVAL, "factor_reuse must be >= 0");
@@ -906,9 +906,9 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     double* r2 = P->dscratch.p + 3 * m;
     // local solve buffers
     if (mixed) {
-        P->Y32.ensure((size_t)E.F.nloc * m);
-        P->Z32.ensure((size_t)E.F.nloc * m);
-        P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+        P->Y32.ensure((size_t)E.F.nloc * (m + 1));
+        P->Z32.ensure((size_t)E.F.nloc * (m + 1));
+        P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * (m + 1));
         if (nested) P->inner.reserve(n, m, std::max(1, o.inner_iters));
         P->v32.ensure(nm);
         P->x32.ensure(nm);
@@ -1035,9 +1035,9 @@ void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_sol
     double* tol = P->dscratch.p + m;
     double* bnorm = P->dscratch.p + 2 * m;
     double* r2 = P->dscratch.p + 3 * m;
-    P->Y32.ensure((size_t)E.F.nloc * m);
-    P->Z32.ensure((size_t)E.F.nloc * m);
-    P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+    P->Y32.ensure((size_t)E.F.nloc * (m + 1));
+    P->Z32.ensure((size_t)E.F.nloc * (m + 1));
+    P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * (m + 1));
     auto Aop = [&](const float2* z, float2* w) {
         timed(P, 0, [&] { spmm_df(n, M->A.row_ptr.p, M->A.col.p, P->Adf.p, nnz, z, w, m, st); });
     };
@@ -1384,9 +1384,9 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
         DecompEntry& E = *P->dec;
         const int64_t n = P->mesh->T.ndof;
         if (P->opts.precision != 0) {
-            P->Y32.ensure((size_t)E.F.nloc * m);
-            P->Z32.ensure((size_t)E.F.nloc * m);
-            P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
+            P->Y32.ensure((size_t)E.F.nloc * (m + 1));
+            P->Z32.ensure((size_t)E.F.nloc * (m + 1));
+            P->upd32.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * (m + 1));
             P->v32.ensure(n * m);
             P->x32.ensure(n * m);
             convert_c128_to_c64(n * m, (const double2*)x_dev, P->v32.p, P->st);
@@ -1558,6 +1558,56 @@ mwi_status mwi_oras_traffic(mwi_problem_t P, int32_t m, double* bytes) {
     });
 }
 
+mwi_status mwi_sweep_levels(mwi_problem_t P, int32_t max_levels, int32_t* n_levels, int64_t* fronts,
+                            int64_t* panel_entries, int64_t* update_rows, int64_t* tiles_fwd, int64_t* tiles_bwd) {
+    return guard([&] {
+        MWI_REQUIRE(P && n_levels && max_levels >= 0, MWI_EINVAL, "bad argument");
+        const Decomposition& D = P->dec->D;
+        const FrontsDev& F = P->dec->F;
+        *n_levels = D.n_levels;
+        for (int l = 0; l < std::min<int>(D.n_levels, max_levels); ++l) {
+            int64_t e = 0, u = 0;
+            for (int q = D.level_ptr[l]; q < D.level_ptr[l + 1]; ++q) {
+                const Front& fr = D.fronts[D.level_fronts[q]];
+                e += (int64_t)fr.p * (fr.p + fr.u);
+                u += fr.u;
+            }
+            if (fronts) fronts[l] = D.level_ptr[l + 1] - D.level_ptr[l];
+            if (panel_entries) panel_entries[l] = e;
+            if (update_rows) update_rows[l] = u;
+            if (tiles_fwd) tiles_fwd[l] = F.tiles128.f_ptr[l + 1] - F.tiles128.f_ptr[l];
+            if (tiles_bwd) tiles_bwd[l] = F.tiles128.p_ptr[l + 1] - F.tiles128.p_ptr[l];
+        }
+    });
+}
+
+mwi_status mwi_recycle_from(mwi_problem_t dst, mwi_problem_t src) {
+    return guard([&] {
+        MWI_REQUIRE(dst && src && dst != src, MWI_EINVAL, "bad argument");
+        MWI_REQUIRE(dst->mesh == src->mesh, MWI_EINVAL, "the problems are on different meshes");
+        MWI_REQUIRE(dst->opts.recycle == 1, MWI_ESTATE, "the destination problem was created without recycle = 1");
+        MWI_REQUIRE(src->have_fwd, MWI_ESTATE, "the source problem holds no forward solutions");
+        const int m = src->m_fwd;
+        MWI_REQUIRE(m <= 32, MWI_EINVAL, "recycling takes at most 32 columns");
+        const int64_t nm = src->mesh->T.ndof * (int64_t)m;
+        // the source's work is complete (calls return after it); order the copy on the destination's stream
+        MWI_CUDA(cudaStreamSynchronize(src->st));
+        dst->U.ensure(nm);
+        MWI_CUDA(cudaMemcpyAsync(dst->U.p, src->U.p, nm * sizeof(double2), cudaMemcpyDeviceToDevice, dst->st));
+        dst->rec_m[0] = m;
+        dst->rec_m[1] = 0;
+        if (src->have_adj) {
+            dst->Lam.ensure(nm);
+            MWI_CUDA(cudaMemcpyAsync(dst->Lam.p, src->Lam.p, nm * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                     dst->st));
+            dst->rec_m[1] = m;
+        }
+        MWI_CUDA(cudaStreamSynchronize(dst->st));
+        dst->have_fwd = false;
+        dst->have_adj = false;
+    });
+}
+
 mwi_status mwi_problem_estimate_bytes(mwi_mesh_t M, const mwi_solver_opts* opts, int32_t n_rhs, int64_t* bytes) {
     return guard([&] {
         MWI_REQUIRE(M && bytes && n_rhs >= 1, MWI_EINVAL, "bad argument");
@@ -1583,7 +1633,7 @@ mwi_status mwi_problem_estimate_bytes(mwi_mesh_t M, const mwi_solver_opts* opts,
         // fields of every column (forward, adjoint, right-hand sides), block copies, residual
         b += 3 * n * mall * 16 + 3 * n * m * 16;
         // local and update vectors of the ORAS application
-        b += (2 * (double)F.nloc + (double)F.upd_rows) * m * fe + 2 * n * m * 8;
+        b += (2 * (double)F.nloc + (double)F.upd_rows) * (m + 1) * fe + 2 * n * m * 8;
         if (o.block_krylov) b += (r + 2) * n * m * 16 + 2 * n * m * 16;
         else if (o.precision == 1) b += ((r + 1) * 2 + r + 2) * n * m * 8 + 3 * 2 * n * m * 8;
         else if (nested) b += (13 + 12 + 1) * n * m * 16 + (o.inner_iters * 2 + 2) * n * m * 8;

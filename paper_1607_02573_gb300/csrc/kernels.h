@@ -164,6 +164,8 @@ template <typename C>
 void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, const SweepCfg& sc,
                         cudaStream_t st);
 int sweep_tile_rows(bool fp32);
+// columns of the ORAS local vectors for m right-hand sides (even for tc 4)
+int sweep_ld(int m, int tc);
 
 // tensor-core sweeps (sweep_tc.cu)
 int64_t tiled_panel_floats(int p, int f);

@@ -25,19 +25,21 @@ template <> __device__ __forceinline__ float2 cvt<float2, float2>(float2 v) { re
 template <> __device__ __forceinline__ float2 cvt<double2, float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 template <> __device__ __forceinline__ double2 cvt<float2, double2>(float2 v) { return make_double2(v.x, v.y); }
 
+// local vectors have ld >= m columns; the columns m..ld-1 are zero
 template <typename In, typename C>
-__global__ void gather_kernel(int64_t nloc, int m, const int32_t* __restrict__ loc2glob, const In* __restrict__ x,
-                              C* __restrict__ Y) {
+__global__ void gather_kernel(int64_t nloc, int m, int ld, const int32_t* __restrict__ loc2glob,
+                              const In* __restrict__ x, C* __restrict__ Y) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= nloc * m) return;
-    int64_t r = e / m;
-    int c = (int)(e - r * m);
-    Y[e] = cvt<In, C>(x[(int64_t)loc2glob[r] * m + c]);
+    if (e >= nloc * ld) return;
+    int64_t r = e / ld;
+    int c = (int)(e - r * ld);
+    Y[e] = c < m ? cvt<In, C>(x[(int64_t)loc2glob[r] * m + c]) : czero<C>();
 }
 
 template <typename C, typename Out>
-__global__ void scatter_kernel(int64_t n, int m, const int64_t* __restrict__ own_ptr, const int32_t* __restrict__ own_row,
-                               const double* __restrict__ own_w, const C* __restrict__ Y, Out* __restrict__ y) {
+__global__ void scatter_kernel(int64_t n, int m, int ld, const int64_t* __restrict__ own_ptr,
+                               const int32_t* __restrict__ own_row, const double* __restrict__ own_w,
+                               const C* __restrict__ Y, Out* __restrict__ y) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * m) return;
     int64_t g = e / m;
@@ -45,7 +47,7 @@ __global__ void scatter_kernel(int64_t n, int m, const int64_t* __restrict__ own
     typedef typename real_of<C>::type R;
     C acc = czero<C>();
     for (int64_t q = own_ptr[g]; q < own_ptr[g + 1]; ++q) {
-        C v = Y[(int64_t)own_row[q] * m + c];
+        C v = Y[(int64_t)own_row[q] * ld + c];
         R w = (R)own_w[q];
         acc.x += w * v.x;
         acc.y += w * v.y;
@@ -53,18 +55,24 @@ __global__ void scatter_kernel(int64_t n, int m, const int64_t* __restrict__ own
     y[e] = cvt<C, Out>(acc);
 }
 
+// columns of the local vectors: the tensor-core sweeps move rows by 16-byte
+// bulk copies, so their rows hold an even number of complex FP32 values (an
+// odd m gets one zero column, which every step leaves zero)
+int sweep_ld(int m, int tc) { return (tc == 4 && (m & 1)) ? m + 1 : m; }
+
 template <typename C, typename In, typename Out>
 static void oras_apply_impl(const FrontsDev& F, const C* ws, const In* x, Out* y, int m, C* Y, C* Z, C* upd,
                             cudaStream_t st, const SweepCfg& sc) {
     const int th = 256;
-    int64_t tot = F.nloc * m;
-    gather_kernel<In, C><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(F.nloc, m, F.loc2glob.p, x, Y);
+    const int ld = sizeof(C) == sizeof(float2) ? sweep_ld(m, sc.tc) : m;
+    int64_t tot = F.nloc * ld;
+    gather_kernel<In, C><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(F.nloc, m, ld, F.loc2glob.p, x, Y);
     MWI_CHECK_LAUNCH();
-    multifrontal_solve<C>(F, ws, Y, Z, upd, m, sc, st);
+    multifrontal_solve<C>(F, ws, Y, Z, upd, ld, sc, st);
     // scatter into the global vector (n = own_ptr size - 1)
     const int64_t n = (int64_t)F.own_ptr.n - 1;
     tot = n * m;
-    scatter_kernel<C, Out><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(n, m, F.own_ptr.p, F.own_row.p,
+    scatter_kernel<C, Out><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(n, m, ld, F.own_ptr.p, F.own_row.p,
                                                                           F.own_w.p, Y, y);
     MWI_CHECK_LAUNCH();
 }
@@ -117,7 +125,8 @@ static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed) {
     const size_t elt = mixed ? sizeof(float2) : sizeof(double2);
-    size_t b = 2 * round256((size_t)F.nloc * m * elt) + round256((size_t)std::max<int64_t>(1, F.upd_rows) * m * elt);
+    const int ld = mixed ? m + (m & 1) : m;
+    size_t b = 2 * round256((size_t)F.nloc * ld * elt) + round256((size_t)std::max<int64_t>(1, F.upd_rows) * ld * elt);
     if (mixed) b += 2 * round256((size_t)n * m * sizeof(float2));
     return b;
 }
@@ -130,10 +139,11 @@ void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const do
                                 "allocation-free entry point holds " + std::to_string(kOrasScratchBytes));
     unsigned char* base = static_cast<unsigned char*>(oras_scratch_address());
     const size_t elt = mixed ? sizeof(float2) : sizeof(double2);
+    const int ld = mixed ? m + (m & 1) : m;
     unsigned char* Yp = base;
-    unsigned char* Zp = Yp + round256((size_t)F.nloc * m * elt);
-    unsigned char* Up = Zp + round256((size_t)F.nloc * m * elt);
-    unsigned char* Vp = Up + round256((size_t)std::max<int64_t>(1, F.upd_rows) * m * elt);
+    unsigned char* Zp = Yp + round256((size_t)F.nloc * ld * elt);
+    unsigned char* Up = Zp + round256((size_t)F.nloc * ld * elt);
+    unsigned char* Vp = Up + round256((size_t)std::max<int64_t>(1, F.upd_rows) * ld * elt);
     unsigned char* Xp = Vp + round256((size_t)n * m * sizeof(float2));
     if (mixed) {
         float2* v32 = reinterpret_cast<float2*>(Vp);

@@ -520,11 +520,12 @@ template <typename C>
 void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int m, const SweepCfg& sc,
                         cudaStream_t st) {
     const int nlev = (int)F.level_ptr.size() - 1;
-    // the tcgen05 engine moves right-hand-side rows by 16-byte bulk copies:
-    // an odd column count takes the mma.sync TF32 engine
-    const bool tc5 = sc.tc == 4 && (m % 2) == 0;
-    const int tc = sc.tc == 4 ? 2 : sc.tc;
+    // the tcgen05 engine moves right-hand-side rows by 16-byte bulk copies
+    // (oras_apply pads the local vectors to an even column count)
+    const bool tc5 = sc.tc == 4;
+    const int tc = sc.tc;
     MWI_REQUIRE(!tc5 || (sc.wt && sc.err), MWI_EINVAL, "internal: tensor-core sweeps without the tiled panels");
+    MWI_REQUIRE(!tc5 || (m % 2) == 0, MWI_EINVAL, "internal: tensor-core sweeps need an even column count");
     for (int l = 0; l < nlev; ++l) {
         launch_gather<C>(F, l, Y, upd, m, st);
         if (tc5) launch_tc_product<C>(F, l, false, ws, Y, Z, upd, m, sc, st);

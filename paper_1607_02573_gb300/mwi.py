@@ -79,6 +79,8 @@ _SIGS = {
     "mwi_factor_stats": [_vp, _i64p, _i64p, _i64p, _dp],
     "mwi_problem_device_bytes": [_vp, _i64p],
     "mwi_problem_estimate_bytes": [_vp, C.POINTER(mwi_solver_opts), C.c_int32, _i64p],
+    "mwi_recycle_from": [_vp, _vp],
+    "mwi_sweep_levels": [_vp, C.c_int32, _i32p, _i64p, _i64p, _i64p, _i64p, _i64p],
     "mwi_oras_traffic": [_vp, C.c_int32, _dp],
     "mwi_update_kappa_device": [_vp, _vp],
     "mwi_misfit_and_gradient_kappa_device": [_vp, _vp, _vp, C.c_double, _dp, _dp, _vp, C.POINTER(mwi_solve_info)],
@@ -297,6 +299,20 @@ class Problem:
         check(st, allow=(MWI_ENOTCONV,) if allow_notconv else ())
         self.info = info
         return J.value, R.value, grad
+
+    def sweep_levels(self):
+        """Per tree level (deepest first): fronts, panel entries, update rows and
+        the 128-row tiles of the forward and backward tensor-core products."""
+        n = C.c_int32()
+        arr = [np.zeros(64, dtype=np.int64) for _ in range(5)]
+        check(mwi_sweep_levels(self.h, 64, C.byref(n), *[_ptr(a, C.c_int64) for a in arr]))
+        names = ["fronts", "panel_entries", "update_rows", "tiles_fwd", "tiles_bwd"]
+        return {k: a[:n.value].tolist() for k, a in zip(names, arr)}
+
+    def recycle_from(self, other):
+        """Take the resident solutions of another problem on the same mesh (a
+        nearby frequency) as this problem's recycled space (mwi_recycle_from)."""
+        check(mwi_recycle_from(self.h, other.h))
 
     def fields(self, which=0):
         """Borrowed device pointer and shape (n, m) of the resident fields."""

@@ -92,9 +92,9 @@ def test_oras_apply_parity(lib, precision, engine, tol, m):
     """engine: complex FP32 sweeps on tensor cores with split TF32 operands (1),
     plain TF32 (2, about 1e-3 relative), CUDA cores (3), or tcgen05 TF32 with
     bulk-copied tiled panels (4: the tensor core truncates the FP32 operands
-    to TF32, up to 2^-10 relative per operand; an odd column count falls back
-    to engine 2).  m: columns -- odd, even, and two 32-column chunks with a
-    ragged second one."""
+    to TF32, up to 2^-10 relative per operand; an odd column count gets one
+    zero padding column).  m: columns -- odd, even, and two 32-column chunks
+    with a ragged second one."""
     case = chamber_case(12, 11)
     mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
     part = dd.rcb_partition(mesh.xyz, mesh.tet, 6)

@@ -196,3 +196,41 @@ def test_recycling_order2(lib):
     assert rel_err(S, ref2["S"]) <= 1e-6
     P.close()
     M.close()
+
+
+@pytest.mark.parametrize("precision,rtol,tol", [(0, 1e-12, 1e-8), (1, 1e-9, 1e-6)])
+def test_recycling_across_nearby_frequencies(lib, chamber, precision, rtol, tol):
+    """The solutions at 1 GHz, handed to the problem at 1.02 GHz
+    (mwi_recycle_from), start its forward and adjoint solves: the results
+    match the direct oracle at 1.02 GHz, in fewer iterations than from zero."""
+    mesh, eps, eps2, tx, rx, M, topo, perm, ref2 = chamber
+    f2 = 1.02e9
+    P1 = lib.Problem(M, eps, FREQ, n_sub=6, precision=precision, rtol=rtol, max_iter=400)
+    P1.forward_solve(tx, rx)
+    S1 = P1.forward_solve(tx, rx)
+    P1.misfit_and_gradient(S1 * 0.9)
+    cold = lib.Problem(M, eps, f2, n_sub=6, precision=precision, rtol=rtol, max_iter=400)
+    cold.forward_solve(tx, rx)
+    it_cold = cold.info.iters_max
+    S_c = cold.forward_solve(tx, rx)
+    J_c, g_c = cold.misfit_and_gradient(S_c * 0.9)
+    it_cold_adj = cold.info.iters_max
+    warm = lib.Problem(M, eps, f2, n_sub=6, precision=precision, rtol=rtol, max_iter=400, recycle=1)
+    warm.recycle_from(P1)
+    S = warm.forward_solve(tx, rx)
+    assert warm.info.iters_max < it_cold, (warm.info.iters_max, it_cold)
+    ref = O.forward(mesh.xyz, topo, eps, f2, tx, rx)
+    assert col_rel_err(warm.fields_host(0), ref["U"][perm]).max() <= tol
+    assert rel_err(S, ref["S"]) <= tol
+    J, g = warm.misfit_and_gradient(S * 0.9)
+    J_o, g_o, _ = O.misfit_and_gradient(mesh.xyz, topo, eps, f2, tx, rx, S * 0.9, fwd=ref)
+    assert abs(J - J_o) <= tol * abs(J_o) and rel_err(g, g_o) <= tol
+    assert warm.info.iters_max <= it_cold_adj
+    # refused without recycle = 1, or from a problem without solutions
+    with pytest.raises(lib.MwiError):
+        cold.recycle_from(P1)
+    fresh = lib.Problem(M, eps, FREQ, n_sub=6, precision=precision, recycle=1)
+    with pytest.raises(lib.MwiError):
+        warm.recycle_from(fresh)
+    for P in (P1, cold, warm, fresh):
+        P.close()
