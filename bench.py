@@ -326,6 +326,12 @@ def run_mine(args, rank, world):
     return mesh, M, results
 
 
+# DRAM bytes of one ORAS apply of the bench workload, summed over its launches
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum (tcgen05 sweeps)
+ORAS_TRAFFIC = {"bytes_per_call": 7.974e9,
+                "source": "ncu DRAM counters of one apply at the bench size, profiles/oras_apply_chamber402k_traffic.md"}
+
+
 def db_bins(S, S_ref, edges=(0.0, -20.0, -60.0)):
     """Largest entrywise relative error of S against S_ref in bins of
     |S_ref| in dB below its largest entry: [0, -20), [-20, -60), below -60."""
@@ -820,7 +826,7 @@ def main():
         "e2e": {"value": round(mx["e2e_value"] * world, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": mx["clocks"],
-        "roofline": roofline(mx, M.ndof, m),
+        "roofline": roofline(mx, M.ndof, m, traffic=ORAS_TRAFFIC if args.engine in (0, 4) else None),
         "kernel_ms_per_step": {k: round(v / mx["steps"], 3) for k, v in
                                zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"], mx["kernel_ms"])},
         "solver": {"fwd": mx["fwd_info"], "adj": mx["adj_info"], "factor": mx["factor"]},
