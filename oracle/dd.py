@@ -226,17 +226,21 @@ class CoarseSpace:
     of the same domain.  The prolongation maps coarse DOFs to fine edge DOFs by
     the fine edge's tangential integral of the coarse field, midpoint rule:
       P[e, E] = N_E(m_e) . (x_hi(e) - x_lo(e)),
-    N_E evaluated in the coarse tet that contains the midpoint m_e (for a
-    midpoint outside the coarse mesh, the candidate tet with the largest
-    smallest barycentric coordinate, i.e. the affine extension of the nearest
-    tet's basis).  Coarse operator A_c = P^T A P (Galerkin; A is complex
-    symmetric, so P^T).  Deflated two-level preconditioner:
+    N_E evaluated in the coarse tet that holds the midpoint m_e, found by
+    brute force over all coarse tets: the lowest-numbered tet whose smallest
+    barycentric coordinate of m_e is >= -1e-12; for a midpoint in no tet
+    (outside the coarse mesh), the lowest-numbered tet whose smallest
+    barycentric coordinate is within 1e-12 of the largest over all tets (the
+    affine extension of the least-outside tet's basis).  Ties go to the lowest
+    tet number, so that rounding and search order cannot change the choice:
+    N_E's normal component jumps across coarse faces, and exact ties are
+    common on structured coarse meshes.  Coarse operator A_c = P^T A P
+    (Galerkin; A is complex symmetric, so P^T).  Deflated two-level
+    preconditioner:
       M_2 r = M_ORAS (r - A Q r) + Q r,   Q = P A_c^{-1} P^T.
     """
 
     def __init__(self, fine_xyz, fine_topo, coarse_xyz, coarse_topo, A, oras):
-        from scipy.spatial import cKDTree
-
         from .fem import bary_gradients
         from .topology import LOCAL_EDGES
 
@@ -250,17 +254,20 @@ class CoarseSpace:
         live = np.nonzero(fdof >= 0)[0]
         mid = 0.5 * (fine_xyz[e[live, 0]] + fine_xyz[e[live, 1]])
         tang = fine_xyz[e[live, 1]] - fine_xyz[e[live, 0]]
-        k = min(12, ctv.shape[0])
-        _, cand = cKDTree(cen).query(mid, k=k)
-        cand = cand.reshape(live.size, k)
-        # barycentric coordinates of every midpoint in every candidate: lambda_a is
-        # affine with gradient G_a and equals 1/4 at the centroid
-        lam = np.einsum("nkad,nkd->nka", G[cand], mid[:, None, :] - cen[cand]) + 0.25
-        mins = lam.min(axis=2)
-        inside = mins >= -1e-12
-        pick = np.where(inside.any(axis=1), inside.argmax(axis=1), mins.argmax(axis=1))
-        t = cand[np.arange(live.size), pick]
-        L = lam[np.arange(live.size), pick]
+        t = np.empty(live.size, dtype=np.int64)
+        L = np.empty((live.size, 4))
+        for a in range(0, live.size, 64):
+            b = min(live.size, a + 64)
+            # barycentric coordinates of every midpoint in every coarse tet:
+            # lambda_q is affine with gradient G_q and equals 1/4 at the centroid
+            lam = np.einsum("tqd,ntd->ntq", G, mid[a:b, None, :] - cen[None, :, :]) + 0.25
+            mins = lam.min(axis=2)
+            inside = mins >= -1e-12
+            near = mins >= mins.max(axis=1, keepdims=True) - 1e-12
+            pick = np.where(inside.any(axis=1), inside.argmax(axis=1), near.argmax(axis=1))
+            t[a:b] = pick
+            L[a:b] = lam[np.arange(b - a), pick]
+        self.located = (fdof[live], t)  # (fine DOF, coarse tet) of every live fine Whitney edge
         rows, cols, vals = [], [], []
         for j, (a, b) in enumerate(LOCAL_EDGES):
             N = L[:, a, None] * G[t, b] - L[:, b, None] * G[t, a]
