@@ -59,6 +59,9 @@ def parse():
                     help="one forward solve instead of the gradient step, for sizing and profiling: "
                          "NXY,NZ,N_SUB,PRECISION[,N_ANT,ORDER,RINGS,MAX_BLOCK,RESTART] "
                          "(defaults 30,28,32,1,32,1,1,64,50: 120,288 tets; RINGS=5 is the 160-antenna layout)")
+    ap.add_argument("--coarse", default=None,
+                    help="with --solve: NXY,NZ of an unjittered coarse chamber whose Whitney space is the coarse "
+                         "space of a two-level ORAS")
     ap.add_argument("--nxy", type=int, default=45)
     ap.add_argument("--nz", type=int, default=42)
     ap.add_argument("--n-ant", type=int, default=32)
@@ -696,6 +699,15 @@ def run_solve(args):
     t1 = time.time()
     P = mwi.Problem(M, eps, FREQ, n_sub=n_sub, precision=prec, rtol=RTOL, max_block=max_block, restart=restart,
                     sweep_engine=args.engine, verbose=2)
+    coarse = None
+    if args.coarse:
+        cxy, cz = [int(v) for v in args.coarse.split(",")]
+        cm = chamber_mesh(cxy, cz, jitter=0.0, permute=False)
+        Mc = mwi.Mesh(cm.xyz, cm.tet, cm.bface_tag)
+        P.set_coarse_space(Mc)
+        Mc.close()
+        coarse = dict(P.coarse_info(), grid=[cxy, cz])
+        P.kernel_times(reset=True)
     t2 = time.time()
     S = P.forward_solve(ants, ants, allow_notconv=True)
     torch.cuda.synchronize()
@@ -709,7 +721,7 @@ def run_solve(args):
             "oras_impl_bytes_per_call": P.oras_traffic(min(32, ants.shape[0])), "solve": info,
             "kernel_ms": dict(zip(["spmm", "oras_apply", "orthogonalisation", "factorisation"],
                                   [round(v, 2) for v in kms.tolist()])),
-            "kernel_calls": kcnt.tolist(), "levels": P.sweep_levels(),
+            "kernel_calls": kcnt.tolist(), "levels": P.sweep_levels(), "coarse": coarse,
             "reciprocity": float(np.linalg.norm(S - S.T) / np.linalg.norm(S))}
     P.close()
     M.close()

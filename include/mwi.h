@@ -239,8 +239,10 @@ const char* mwi_last_error(void);
  * iteration). */
 mwi_status mwi_spmm_device(mwi_problem_t prob, const double* x_dev, double* y_dev, int32_t m);
 
-/* y = M^-1 x with the ORAS preconditioner of Eq. ORAS in the problem's
- * precision (x and y in FP64; converted around the FP32 factors if MIXED). */
+/* y = M^-1 x with the problem's preconditioner in its precision (x and y in
+ * FP64; converted around the FP32 factors if MIXED): the ORAS of Eq. ORAS, or
+ * the two-level ORAS once mwi_set_coarse_space has given the problem a
+ * coarse space. */
 mwi_status mwi_oras_apply_device(mwi_problem_t prob, const double* x_dev, double* y_dev,
                                  int32_t m);
 
@@ -361,6 +363,45 @@ mwi_status mwi_sweep_levels(mwi_problem_t prob, int32_t max_levels, int32_t* n_l
  * returns when done; dst's previous fields are dropped.  The two handles must
  * not be in use by other threads during the call. */
 mwi_status mwi_recycle_from(mwi_problem_t dst, mwi_problem_t src);
+
+/* Two-level ORAS (Section 7: a coarse space keeps the iteration count of the
+ * one-level method from growing with the number of subdomains).  The coarse
+ * space is the lowest-order Whitney space of coarse_mesh (order 1, covering
+ * the same domain; its PEC faces remove coarse DOFs as in any mesh).
+ * Prolongation P [n x n_c], real: the fine edge e's tangential integral of a
+ * coarse field by the midpoint rule, P[e,E] = N_E(m_e) . (x_hi - x_lo), with
+ * N_E evaluated in the lowest-numbered coarse tet that holds the midpoint m_e
+ * (smallest barycentric coordinate >= -1e-12); for a midpoint outside the
+ * coarse mesh, in the lowest-numbered tet whose smallest barycentric
+ * coordinate is within 1e-12 of the largest over all tets (the affine
+ * extension of the least-outside tet's basis); only the fine Whitney DOFs get
+ * rows. 
+ * Coarse operator A_c = P^T A P (Galerkin; A complex symmetric), factorised as
+ * one dense front in the problem's factor precision.  Preconditioner (every
+ * solve of the problem, and mwi_oras_apply_device):
+ *   M_2 r = M_ORAS (r - A Q r) + Q r,   Q = P A_c^{-1} P^T.
+ * A_c and its factors follow every later refactorisation (new eps_r, kappa).
+ * Setup: P and the pattern of A_c on the host cores, A_c's values from a host
+ * copy of A (host cores), the factorisation on the problem's stream; returns
+ * when done.  n_c <= 16384 (else MWI_EINVAL; the dense front takes n_c^2
+ * complex entries twice).  coarse_mesh may be destroyed afterwards.  NULL
+ * removes the coarse space.  mwi_oras_apply_device_noalloc refuses a problem
+ * with a coarse space (MWI_EINVAL). */
+mwi_status mwi_set_coarse_space(mwi_problem_t prob, mwi_mesh_t coarse_mesh);
+
+/* Sizes of the problem's coarse space (all 0 without one): n_c coarse DOFs,
+ * entries of P and of A_c, host+device setup time of the last (re)build of
+ * A_c and its factors, and the factorisation's replaced pivots.  Any pointer
+ * may be NULL. */
+mwi_status mwi_coarse_info(mwi_problem_t prob, int64_t* n_coarse, int64_t* nnz_p, int64_t* nnz_ac,
+                           double* setup_ms, int32_t* n_perturbed);
+
+/* Host copies of P (CSR: p_rp [n+1], p_col [nnz_p], p_val [nnz_p]) and of A_c
+ * (CSR: ac_rp [n_c+1], ac_col [nnz_ac], ac_val [2*nnz_ac] interleaved complex),
+ * columns ascending in every row.  Any pointer may be NULL; MWI_ESTATE
+ * without a coarse space. */
+mwi_status mwi_coarse_operator(mwi_problem_t prob, int64_t* p_rp, int32_t* p_col, double* p_val, int64_t* ac_rp,
+                               int32_t* ac_col, double* ac_val);
 
 /* Upper estimate of the device bytes a problem on this mesh with these
  * options will hold after solves of n_rhs transmitters (its operator,

@@ -36,6 +36,36 @@ struct DecompEntry {
     std::once_flag ut_once[2];
 };
 
+// Two-level ORAS of one problem: the prolongation and the pattern of
+// A_c = P^T A P (host), A_c as one dense front with its factors in the
+// problem's precision, and the scratch of the coarse solves and corrections.
+struct CoarseLevel {
+    CoarseHost H;
+    Decomposition D;
+    FrontsDev F;
+    UpdateTiles ut;
+    CoarseDev dev;
+    std::vector<double2> Aval_h, Ac_h;
+    DevBuf<double2> Ac;
+    DevBuf<double2> ws64, inv64, sch64[2];
+    DevBuf<float2> ws32, inv32, sch32[2];
+    DevBuf<double2> Y64, Z64, upd64, ct64, cq64, q64, w64;
+    DevBuf<float2> Y32, Z32, upd32, ct32, cq32, q32, w32;
+    DevBuf<int> perturbed;
+    int n_perturbed = 0;
+    double setup_ms = 0;
+    size_t bytes() const {
+        size_t b = dev.P_rp.bytes() + dev.PT_rp.bytes() + dev.P_col.bytes() + dev.PT_col.bytes() +
+                   dev.P_val.bytes() + dev.PT_val.bytes() + Ac.bytes() + ws64.bytes() + inv64.bytes() +
+                   ws32.bytes() + inv32.bytes() + Y64.bytes() + Z64.bytes() + upd64.bytes() + ct64.bytes() +
+                   cq64.bytes() + q64.bytes() + w64.bytes() + Y32.bytes() + Z32.bytes() + upd32.bytes() +
+                   ct32.bytes() + cq32.bytes() + q32.bytes() + w32.bytes() + perturbed.bytes() + ut.tiles.bytes() +
+                   ut.rtiles.bytes();
+        for (int k = 0; k < 2; ++k) b += sch64[k].bytes() + sch32[k].bytes();
+        return b;
+    }
+};
+
 // The factorisation's trailing-update tiles, in its consumption order: per
 // level, per chunk of at most 65535 fronts, per step k of nb pivot columns,
 // the lower-triangle tiles of every front of the chunk with k < p.
@@ -151,6 +181,7 @@ struct mwi_problem {
     DevBuf<double> rx_sign_d, tx_sign_d;
     DevBuf<double2> cur_d, S_d, Smeas_d, r_d, grad_d;
     DevBuf<double> w_d, J_d;
+    std::unique_ptr<CoarseLevel> coarse;  // two-level ORAS (mwi_set_coarse_space)
     int n_rx = 0;
     double setup_ms = 0;
     int inner_total = 0;
@@ -178,6 +209,7 @@ struct mwi_problem {
                    kappa.bytes() + Mk.bytes() + grad_tw.bytes() + p1_partial.bytes() + nonfinite.bytes() +
                    wt.bytes() + sweep_err.bytes();
         for (int k = 0; k < 2; ++k) b += sch64[k].bytes() + sch32[k].bytes();
+        if (coarse) b += coarse->bytes();
         return b;
     }
 };
@@ -355,6 +387,8 @@ void ensure_global(mwi_mesh* M) {
     M->have_A = true;
 }
 
+void upload_fronts(const Decomposition& D, FrontsDev& F, cudaStream_t st);
+
 std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     std::vector<int32_t> key;
     if (o.part) key.assign(o.part, o.part + M->T.nt);
@@ -372,7 +406,14 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
     upload_slots(D.B, E->B, st);
     up(E->fu_face, D.B_faces.face, st);
     up(E->fu_tet, D.B_faces.tet, st);
-    FrontsDev& F = E->F;
+    upload_fronts(D, E->F, st);
+    M->cache.push_back(E);
+    return E;
+}
+
+// the multifrontal structure of a decomposition on the device: fronts, extend-add
+// and assembly lists, the sweeps' tile lists and the tiled-panel offsets
+void upload_fronts(const Decomposition& D, FrontsDev& F, cudaStream_t st) {
     const size_t nf = D.fronts.size();
     F.nfronts = (int64_t)nf;
     std::vector<int32_t> start(nf), p(nf), u(nf), parent(nf), sub(nf);
@@ -563,8 +604,132 @@ std::shared_ptr<DecompEntry> get_decomp(mwi_mesh* M, const mwi_solver_opts& o) {
         up(F.inv_off, io, st);
     }
     MWI_CUDA(cudaStreamSynchronize(st));
-    M->cache.push_back(E);
-    return E;
+}
+
+// A_c = P^T A P for the problem's current A (Galerkin product on the host
+// cores from a copy of A's values), then A_c's factorisation on the device
+void coarse_refresh(mwi_problem* P) {
+    CoarseLevel& L = *P->coarse;
+    mwi_mesh* M = P->mesh;
+    cudaStream_t st = P->st;
+    const double t0 = now_ms();
+    const int64_t nnz = M->A.nnz;
+    L.Aval_h.resize(nnz);
+    MWI_CUDA(cudaMemcpyAsync(L.Aval_h.data(), P->Aval.p, nnz * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    MWI_CUDA(cudaStreamSynchronize(st));
+    coarse_values(M->A_host.row_ptr, M->A_host.col, L.Aval_h.data(), L.H, L.Ac_h);
+    L.Ac.ensure(L.Ac_h.size());
+    MWI_CUDA(cudaMemcpyAsync(L.Ac.p, L.Ac_h.data(), L.Ac_h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    L.perturbed.ensure(1);
+    MWI_CUDA(cudaMemsetAsync(L.perturbed.p, 0, sizeof(int), st));
+    if (P->opts.precision != 0) {
+        L.ws32.ensure(L.F.ws_total());
+        L.inv32.ensure(std::max<int64_t>(1, L.F.inv_entries));
+        for (int k = 0; k < 2; ++k) L.sch32[k].ensure(1);
+        float2* sch[2] = {L.sch32[0].p, L.sch32[1].p};
+        factorize_fronts<float2>(L.F, L.ut, L.Ac.p, L.ws32.p, sch, L.inv32.p, L.perturbed.p, st);
+    } else {
+        L.ws64.ensure(L.F.ws_total());
+        L.inv64.ensure(std::max<int64_t>(1, L.F.inv_entries));
+        for (int k = 0; k < 2; ++k) L.sch64[k].ensure(1);
+        double2* sch[2] = {L.sch64[0].p, L.sch64[1].p};
+        factorize_fronts<double2>(L.F, L.ut, L.Ac.p, L.ws64.p, sch, L.inv64.p, L.perturbed.p, st);
+    }
+    MWI_CUDA(cudaMemcpyAsync(&L.n_perturbed, L.perturbed.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MWI_CUDA(cudaStreamSynchronize(st));
+    L.setup_ms = now_ms() - t0;
+}
+
+// the FP32 copy of A used by the mixed two-level correction (the nested path
+// assembles it anyway)
+void refresh_a32(mwi_problem* P) {
+    if (!P->coarse || P->opts.precision != 1) return;
+    const int64_t nnz = P->mesh->A.nnz;
+    P->Aval32.ensure(nnz);
+    convert_c128_to_c64(nnz, P->Aval.p, P->Aval32.p, P->st);
+}
+
+void set_coarse(mwi_problem* P, mwi_mesh* Mc) {
+    if (!Mc) {
+        MWI_CUDA(cudaStreamSynchronize(P->st));
+        P->coarse.reset();
+        return;
+    }
+    mwi_mesh* M = P->mesh;
+    cudaStream_t st = P->st;
+    const double t0 = now_ms();
+    std::unique_ptr<CoarseLevel> L(new CoarseLevel());
+    build_prolongation(M->T, Mc->T, L->H);
+    coarse_pattern(M->A_host.row_ptr, M->A_host.col, L->H);
+    dense_front_decomposition(L->H, L->D);
+    upload_fronts(L->D, L->F, st);
+    CoarseDev& cd = L->dev;
+    cd.n = L->H.n;
+    cd.nc = L->H.nc;
+    up(cd.P_rp, L->H.P_rp, st);
+    up(cd.P_col, L->H.P_col, st);
+    up(cd.P_val, L->H.P_val, st);
+    up(cd.PT_rp, L->H.PT_rp, st);
+    up(cd.PT_col, L->H.PT_col, st);
+    up(cd.PT_val, L->H.PT_val, st);
+    const bool fp32 = P->opts.precision != 0;
+    build_update_tiles(L->D, factor_block_cols(fp32), factor_tile_rows(fp32), L->ut, st);
+    MWI_CUDA(cudaStreamSynchronize(st));
+    P->coarse = std::move(L);
+    try {
+        coarse_refresh(P);
+        refresh_a32(P);
+        MWI_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        P->coarse.reset();
+        throw;
+    }
+    P->coarse->setup_ms = now_ms() - t0;
+}
+
+// y = M x for the problem's preconditioner: the one-level ORAS (one_level),
+// or the deflated two-level ORAS when a coarse space is set
+template <typename C>
+void precondition(mwi_problem* P, const C* x, C* y, int m, const std::function<void(const C*, C*)>& one_level) {
+    if (!P->coarse) {
+        one_level(x, y);
+        return;
+    }
+    CoarseLevel& L = *P->coarse;
+    mwi_mesh* M = P->mesh;
+    cudaStream_t st = P->st;
+    const int64_t n = L.dev.n, nc = L.dev.nc;
+    TwoLevelScratch<C> s;
+    if constexpr (std::is_same<C, float2>::value) {
+        L.ct32.ensure(nc * m);
+        L.cq32.ensure(nc * m);
+        L.q32.ensure(n * m);
+        L.w32.ensure(n * m);
+        L.Y32.ensure(nc * (m + 1));
+        L.Z32.ensure(nc * (m + 1));
+        L.upd32.ensure(1);
+        s = {L.ct32.p, L.cq32.p, L.q32.p, L.w32.p};
+        // exact coarse solve on the FP32 tensor cores (3xTF32 products)
+        SweepCfg sc;
+        sc.tc = 1;
+        auto cs = [&](const float2* t, float2* c) {
+            oras_apply<float2>(L.F, L.ws32.p, nullptr, nullptr, m, L.Y32.p, L.Z32.p, L.upd32.p, st, t, c, sc);
+        };
+        two_level_apply<float2>(L.dev, x, y, m, s, cs, one_level, M->A.row_ptr.p, M->A.col.p, P->Aval32.p, st);
+    } else {
+        L.ct64.ensure(nc * m);
+        L.cq64.ensure(nc * m);
+        L.q64.ensure(n * m);
+        L.w64.ensure(n * m);
+        L.Y64.ensure(nc * m);
+        L.Z64.ensure(nc * m);
+        L.upd64.ensure(1);
+        s = {L.ct64.p, L.cq64.p, L.q64.p, L.w64.p};
+        auto cs = [&](const double2* t, double2* c) {
+            oras_apply<double2>(L.F, L.ws64.p, t, c, m, L.Y64.p, L.Z64.p, L.upd64.p, st);
+        };
+        two_level_apply<double2>(L.dev, x, y, m, s, cs, one_level, M->A.row_ptr.p, M->A.col.p, P->Aval.p, st);
+    }
 }
 
 // assemble A and B_i values for the current eps, then factorise
@@ -590,6 +755,7 @@ void numeric_setup(mwi_problem* P, bool refactor = true) {
         split_c128(M->A.nnz, P->Aval.p, P->Adf.p, st);
     }
     DecompEntry& E = *P->dec;
+    refresh_a32(P);
     if (!refactor) {
         MWI_CUDA(cudaStreamSynchronize(st));
         P->setup_ms = now_ms() - t0;
@@ -636,6 +802,7 @@ void numeric_setup(mwi_problem* P, bool refactor = true) {
     }
     MWI_CUDA(cudaMemcpyAsync(&P->n_perturbed, P->perturbed.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     MWI_CUDA(cudaStreamSynchronize(st));
+    if (P->coarse) coarse_refresh(P);
     P->setup_ms = now_ms() - t0;
     (void)T;
 }
@@ -925,14 +1092,18 @@ void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_
     };
     auto M32 = [&](const float2* x, float2* y) {
         timed(P, 1, [&] {
-            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, x, y,
-                               sweep_cfg(P));
+            precondition<float2>(P, x, y, m, [&](const float2* a, float2* b) {
+                oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, a, b,
+                                   sweep_cfg(P));
+            });
         });
     };
     auto M64 = [&](const double2* x, double2* y) {
         if (!mixed) {
             timed(P, 1, [&] {
-                oras_apply<double2>(E.F, P->ws64.p, x, y, m, P->Y64.p, P->Z64.p, P->upd64.p, st);
+                precondition<double2>(P, x, y, m, [&](const double2* a, double2* b) {
+                    oras_apply<double2>(E.F, P->ws64.p, a, b, m, P->Y64.p, P->Z64.p, P->upd64.p, st);
+                });
             });
             return;
         }
@@ -1043,8 +1214,10 @@ void solve_block_df(mwi_problem* P, const double2* B, double2* X, int m, mwi_sol
     };
     auto Mop = [&](const float2* v, float2* z) {
         timed(P, 1, [&] {
-            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, v, z,
-                               sweep_cfg(P));
+            precondition<float2>(P, v, z, m, [&](const float2* a, float2* b) {
+                oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, st, a, b,
+                                   sweep_cfg(P));
+            });
         });
     };
     G.timer = [P](int slot, const std::function<void()>& fn) { timed(P, slot, fn); };
@@ -1390,15 +1563,18 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
             P->v32.ensure(n * m);
             P->x32.ensure(n * m);
             convert_c128_to_c64(n * m, (const double2*)x_dev, P->v32.p, P->st);
-            oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, P->st, P->v32.p,
-                               P->x32.p, sweep_cfg(P));
+            precondition<float2>(P, P->v32.p, P->x32.p, m, [&](const float2* a, float2* b) {
+                oras_apply<float2>(E.F, P->ws32.p, nullptr, nullptr, m, P->Y32.p, P->Z32.p, P->upd32.p, P->st, a, b,
+                                   sweep_cfg(P));
+            });
             convert_c64_to_c128(n * m, P->x32.p, (double2*)y_dev, P->st);
         } else {
             P->Y64.ensure((size_t)E.F.nloc * m);
             P->Z64.ensure((size_t)E.F.nloc * m);
             P->upd64.ensure((size_t)std::max<int64_t>(1, E.F.upd_rows) * m);
-            oras_apply<double2>(E.F, P->ws64.p, (const double2*)x_dev, (double2*)y_dev, m, P->Y64.p, P->Z64.p,
-                                P->upd64.p, P->st);
+            precondition<double2>(P, (const double2*)x_dev, (double2*)y_dev, m, [&](const double2* a, double2* b) {
+                oras_apply<double2>(E.F, P->ws64.p, a, b, m, P->Y64.p, P->Z64.p, P->upd64.p, P->st);
+            });
         }
         MWI_CUDA(cudaStreamSynchronize(P->st));
         check_sweep_error(P);
@@ -1408,6 +1584,8 @@ mwi_status mwi_oras_apply_device(mwi_problem_t P, const double* x_dev, double* y
 mwi_status mwi_oras_apply_device_noalloc(mwi_problem_t P, const double* x_dev, double* y_dev, int32_t m) {
     return guard([&] {
         MWI_REQUIRE(P && x_dev && y_dev && m >= 1, MWI_EINVAL, "bad argument");
+        MWI_REQUIRE(!P->coarse, MWI_EINVAL,
+                    "the allocation-free entry point applies the one-level ORAS only; this problem has a coarse space");
         DecompEntry& E = *P->dec;
         const bool mixed = P->opts.precision != 0;
         const void* ws = mixed ? (const void*)P->ws32.p : (const void*)P->ws64.p;
@@ -1660,6 +1838,47 @@ mwi_status mwi_kernel_times(mwi_problem_t P, double* ms, int64_t* counts, int32_
             if (ms) ms[k] = P->t_ms[k];
             if (counts) counts[k] = P->t_cnt[k];
             if (reset) { P->t_ms[k] = 0; P->t_cnt[k] = 0; }
+        }
+    });
+}
+
+mwi_status mwi_set_coarse_space(mwi_problem_t P, mwi_mesh_t Mc) {
+    return guard([&] {
+        MWI_REQUIRE(P, MWI_EINVAL, "null problem");
+        set_coarse(P, Mc);
+    });
+}
+
+mwi_status mwi_coarse_info(mwi_problem_t P, int64_t* n_coarse, int64_t* nnz_p, int64_t* nnz_ac, double* setup_ms,
+                           int32_t* n_perturbed) {
+    return guard([&] {
+        MWI_REQUIRE(P, MWI_EINVAL, "null problem");
+        const CoarseLevel* L = P->coarse.get();
+        if (n_coarse) *n_coarse = L ? L->H.nc : 0;
+        if (nnz_p) *nnz_p = L ? (int64_t)L->H.P_col.size() : 0;
+        if (nnz_ac) *nnz_ac = L ? (int64_t)L->H.Ac_col.size() : 0;
+        if (setup_ms) *setup_ms = L ? L->setup_ms : 0.0;
+        if (n_perturbed) *n_perturbed = L ? L->n_perturbed : 0;
+    });
+}
+
+mwi_status mwi_coarse_operator(mwi_problem_t P, int64_t* p_rp, int32_t* p_col, double* p_val, int64_t* ac_rp,
+                               int32_t* ac_col, double* ac_val) {
+    return guard([&] {
+        MWI_REQUIRE(P, MWI_EINVAL, "null problem");
+        MWI_REQUIRE(P->coarse, MWI_ESTATE, "the problem has no coarse space");
+        const CoarseHost& H = P->coarse->H;
+        if (p_rp) std::copy(H.P_rp.begin(), H.P_rp.end(), p_rp);
+        if (p_col) std::copy(H.P_col.begin(), H.P_col.end(), p_col);
+        if (p_val) std::copy(H.P_val.begin(), H.P_val.end(), p_val);
+        if (ac_rp) std::copy(H.Ac_rp.begin(), H.Ac_rp.end(), ac_rp);
+        if (ac_col) std::copy(H.Ac_col.begin(), H.Ac_col.end(), ac_col);
+        if (ac_val) {
+            const std::vector<double2>& v = P->coarse->Ac_h;
+            for (size_t k = 0; k < v.size(); ++k) {
+                ac_val[2 * k] = v[k].x;
+                ac_val[2 * k + 1] = v[k].y;
+            }
         }
     });
 }

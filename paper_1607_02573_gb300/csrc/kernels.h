@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "common.h"
@@ -182,6 +183,26 @@ static const size_t kOrasScratchBytes = (size_t)32 << 20;
 size_t oras_noalloc_bytes(const FrontsDev& F, int64_t n, int m, bool mixed);
 void oras_apply_noalloc(const FrontsDev& F, const void* ws, bool mixed, const double2* x, double2* y, int m,
                         int64_t n, cudaStream_t st, const SweepCfg& sc = SweepCfg());
+
+// ---- two-level ORAS (twolevel.cu): prolongation P [n][nc] and its transpose (CSR, real)
+struct CoarseDev {
+    int64_t n = 0, nc = 0;
+    DevBuf<int64_t> P_rp, PT_rp;
+    DevBuf<int32_t> P_col, PT_col;
+    DevBuf<double> P_val, PT_val;
+};
+// scratch of one application: coarse vectors ct, cq [nc][m]; fine vectors q, w [n][m]
+template <typename C>
+struct TwoLevelScratch {
+    C *ct = nullptr, *cq = nullptr, *q = nullptr, *w = nullptr;
+};
+// y = M_ORAS (x - A Q x) + Q x with Q = P A_c^{-1} P^T; coarse_solve(t, c): c = A_c^{-1} t,
+// one_level(w, z): z = M_ORAS w; A in CSR with int32 row pointers
+template <typename C>
+void two_level_apply(const CoarseDev& cd, const C* x, C* y, int m, const TwoLevelScratch<C>& s,
+                     const std::function<void(const C*, C*)>& coarse_solve,
+                     const std::function<void(const C*, C*)>& one_level, const int32_t* A_rp, const int32_t* A_col,
+                     const C* A_val, cudaStream_t st);
 
 // ---- nodal (P1) permittivity parameter (p1.cu)
 struct Topology;

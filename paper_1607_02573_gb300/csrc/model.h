@@ -3,6 +3,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <vector_types.h>
 
 #include <vector>
 
@@ -126,6 +127,24 @@ struct Decomposition {
     double factor_flops = 0;            // real flops of the numeric factorisation
     int32_t max_front = 0;
 };
+
+// Two-level ORAS (coarse.cpp): the prolongation P from a coarse mesh's
+// Whitney space to the fine DOFs (CSR, and its transpose), and the pattern of
+// the Galerkin operator A_c = P^T A P.
+struct CoarseHost {
+    int64_t n = 0, nc = 0;
+    std::vector<int64_t> P_rp, PT_rp, Ac_rp;
+    std::vector<int32_t> P_col, PT_col, Ac_col;
+    std::vector<double> P_val, PT_val;
+};
+void build_prolongation(const Topology& fine, const Topology& coarse, CoarseHost& out);
+void coarse_pattern(const std::vector<int64_t>& A_rp, const std::vector<int32_t>& A_col, CoarseHost& C);
+// A_c values in the pattern's order from A's values (A_rp/A_col: A's CSR)
+void coarse_values(const std::vector<int64_t>& A_rp, const std::vector<int32_t>& A_col, const double2* A_val,
+                   const CoarseHost& C, std::vector<double2>& out);
+// A_c as a decomposition with one subdomain and one dense front (amap_slot
+// indexes A_c's values)
+void dense_front_decomposition(const CoarseHost& C, Decomposition& D);
 
 // Result of the symbolic analysis of one subdomain (local front ids).
 struct LocalFront {

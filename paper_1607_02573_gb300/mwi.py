@@ -87,6 +87,9 @@ _SIGS = {
     "mwi_normalised_weights": [_dp, C.c_int64, _dp],
     "mwi_kernel_times": [_vp, _dp, _i64p, C.c_int32],
     "mwi_misfit": [_vp, _dp, _dp, _dp],
+    "mwi_set_coarse_space": [_vp, _vp],
+    "mwi_coarse_info": [_vp, _i64p, _i64p, _i64p, _dp, _i32p],
+    "mwi_coarse_operator": [_vp, _i64p, _i32p, _dp, _i64p, _i32p, _dp],
 }
 EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
@@ -313,6 +316,36 @@ class Problem:
         """Take the resident solutions of another problem on the same mesh (a
         nearby frequency) as this problem's recycled space (mwi_recycle_from)."""
         check(mwi_recycle_from(self.h, other.h))
+
+    def set_coarse_space(self, coarse_mesh):
+        """Two-level ORAS with the lowest-order Whitney space of coarse_mesh
+        (a Mesh of order 1) as coarse space; None removes it."""
+        check(mwi_set_coarse_space(self.h, coarse_mesh.h if coarse_mesh is not None else None))
+
+    def coarse_info(self):
+        nc, nnz_p, nnz_ac = C.c_int64(), C.c_int64(), C.c_int64()
+        ms = C.c_double()
+        npert = C.c_int32()
+        check(mwi_coarse_info(self.h, C.byref(nc), C.byref(nnz_p), C.byref(nnz_ac), C.byref(ms), C.byref(npert)))
+        return dict(n_coarse=nc.value, nnz_p=nnz_p.value, nnz_ac=nnz_ac.value, setup_ms=ms.value,
+                    n_perturbed=npert.value)
+
+    def coarse_operator(self):
+        """(P, A_c) as scipy CSR matrices (library DOF order on both meshes)."""
+        import scipy.sparse as sp
+        info = self.coarse_info()
+        n, nc = self.mesh.ndof, info["n_coarse"]
+        p_rp = np.empty(n + 1, dtype=np.int64)
+        p_col = np.empty(info["nnz_p"], dtype=np.int32)
+        p_val = np.empty(info["nnz_p"], dtype=np.float64)
+        a_rp = np.empty(nc + 1, dtype=np.int64)
+        a_col = np.empty(info["nnz_ac"], dtype=np.int32)
+        a_val = np.empty(info["nnz_ac"], dtype=np.complex128)
+        check(mwi_coarse_operator(self.h, _ptr(p_rp, C.c_int64), _ptr(p_col, C.c_int32), _ptr(p_val, C.c_double),
+                                  _ptr(a_rp, C.c_int64), _ptr(a_col, C.c_int32),
+                                  _ptr(a_val.view(np.float64), C.c_double)))
+        return (sp.csr_matrix((p_val, p_col, p_rp), shape=(n, nc)),
+                sp.csr_matrix((a_val, a_col, a_rp), shape=(nc, nc)))
 
     def fields(self, which=0):
         """Borrowed device pointer and shape (n, m) of the resident fields."""
