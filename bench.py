@@ -59,6 +59,9 @@ def parse():
                     help="one forward solve instead of the gradient step, for sizing and profiling: "
                          "NXY,NZ,N_SUB,PRECISION[,N_ANT,ORDER,RINGS,MAX_BLOCK,RESTART] "
                          "(defaults 30,28,32,1,32,1,1,64,50: 120,288 tets; RINGS=5 is the 160-antenna layout)")
+    ap.add_argument("--two-level", default="12,11",
+                    help="NXY,NZ of the coarse chamber of the two-level ORAS measurement on the main line "
+                         "(empty: skip)")
     ap.add_argument("--coarse", default=None,
                     help="with --solve: NXY,NZ of an unjittered coarse chamber whose Whitney space is the coarse "
                          "space of a two-level ORAS")
@@ -256,6 +259,7 @@ def run_mine(args, rank, world):
 
     if args.only_mixed:
         args.nested_steps = args.fp64_steps = args.recycle_steps = args.block_steps = args.p1_steps = 0
+        args.two_level = ""
         args.requests = 2
         args.no_cpu_baseline = True
     results["mixed"] = one_arm(1, args.steps, args.warmup, max(2, args.requests))
@@ -326,13 +330,47 @@ def run_mine(args, rank, world):
                                  "normalised misfit, gradient penalty alpha = 1e-3): update_kappa (P1 masses, "
                                  "assembly, factorisation), forward and adjoint solves, vertex gradient"}
         P.close()
+    # two-level ORAS: one forward solve of the 32 transmitters with the
+    # one-level preconditioner and with a coarse space (Whitney elements of an
+    # unjittered coarse chamber), at the bench's 64 subdomains and at 1,024
+    if args.two_level:
+        from synthetic import chamber_mesh
+        cxy, cz = [int(v) for v in args.two_level.split(",")]
+        cm = chamber_mesh(cxy, cz, jitter=0.0, permute=False)
+        Mc = mwi.Mesh(cm.xyz, cm.tet, cm.bface_tag)
+        results["two_level"] = {"coarse_grid": [cxy, cz], "runs": []}
+        for ns in (64, 1024):
+            P = mwi.Problem(M, eps_d, FREQ, stream=stream, n_sub=ns, precision=1, rtol=RTOL, verbose=2,
+                            max_iter=500, nd_leaf=args.nd_leaf, sweep_engine=args.engine)
+            for coarse in (False, True):
+                if coarse:
+                    P.set_coarse_space(Mc)
+                P.forward_solve(ants, ants)
+                P.kernel_times(reset=True)
+                torch.cuda.synchronize()
+                e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                e0.record(stream)
+                P.forward_solve(ants, ants)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                kms, kcnt = P.kernel_times(reset=True)
+                info = P.info.as_dict()
+                run = {"n_sub": ns, "coarse": coarse, "iterations": info["iters_max"],
+                       "forward_ms": round(e0.elapsed_time(e1), 2), "converged": info["n_converged"],
+                       "oras_apply_ms": round(float(kms[1]) / max(1, int(kcnt[1])), 3)}
+                if coarse:
+                    ci = P.coarse_info()
+                    run.update(n_coarse=ci["n_coarse"], coarse_setup_ms=round(ci["setup_ms"], 1))
+                results["two_level"]["runs"].append(run)
+            P.close()
+        Mc.close()
     return mesh, M, results
 
 
 # DRAM bytes of one ORAS apply of the bench workload, summed over its launches
-# from ncu's dram__bytes_read.sum + dram__bytes_write.sum (tcgen05 sweeps)
-ORAS_TRAFFIC = {"bytes_per_call": 7.974e9,
-                "source": "ncu DRAM counters of one apply at the bench size, profiles/oras_apply_chamber402k_traffic.md"}
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum; None until the
+# counters are taken again for the current kernels
+ORAS_TRAFFIC = None
 
 
 def db_bins(S, S_ref, edges=(0.0, -20.0, -60.0)):
@@ -874,7 +912,12 @@ def main():
                                                      R["reuse"]["kernel_ms"])},
                           "what": "as krylov_recycling, with factor_reuse = 2: two of every three eps_r updates "
                                   "keep the previous subdomain factors as the preconditioner"}
-                      if R.get("reuse") else None},
+                      if R.get("reuse") else None,
+                      "two_level_oras": dict(R["two_level"], what=(
+                          "one forward solve of the 32 transmitters (mixed path, rtol 1e-6) with the one-level "
+                          "ORAS and with the deflated two-level ORAS, the coarse space being the Whitney "
+                          "elements of an unjittered coarse chamber; oras_apply_ms includes the coarse "
+                          "correction")) if R.get("two_level") else None},
     }
     if R["fp64"]:
         f = R["fp64"]

@@ -12,6 +12,7 @@
 // paper notes for multiple vectors (Section 3).  Vectors are row-major [rows][m].
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "common.h"
 #include "gmres.h"
@@ -55,6 +56,43 @@ __global__ void scatter_kernel(int64_t n, int m, int ld, const int64_t* __restri
     y[e] = cvt<C, Out>(acc);
 }
 
+// The same two steps for complex FP32 vectors with an even column count, two
+// columns (16 bytes) per thread: a block of (threads per row) x (rows), so no
+// thread divides by the row length
+__global__ void gather2_kernel(int64_t nloc, int h, int ldh, const int32_t* __restrict__ loc2glob,
+                               const float4* __restrict__ x, float4* __restrict__ Y) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
+    if (r >= nloc) return;
+    const int64_t g = loc2glob[r];
+    for (int c = threadIdx.x; c < ldh; c += blockDim.x)
+        Y[r * ldh + c] = c < h ? x[g * h + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void scatter2_kernel(int64_t n, int h, int ldh, const int64_t* __restrict__ own_ptr,
+                                const int32_t* __restrict__ own_row, const double* __restrict__ own_w,
+                                const float4* __restrict__ Y, float4* __restrict__ y) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
+    if (g >= n) return;
+    const int64_t q0 = own_ptr[g], q1 = own_ptr[g + 1];
+    for (int c = threadIdx.x; c < h; c += blockDim.x) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t q = q0; q < q1; ++q) {
+            const float4 v = Y[(int64_t)own_row[q] * ldh + c];
+            const float w = (float)own_w[q];
+            acc.x += w * v.x;
+            acc.y += w * v.y;
+            acc.z += w * v.z;
+            acc.w += w * v.w;
+        }
+        y[g * h + c] = acc;
+    }
+}
+
+static dim3 pair_block(int h) {
+    const int hx = std::max(1, std::min(h, 256));
+    return dim3(hx, 256 / hx);
+}
+
 // columns of the local vectors: the tensor-core sweeps move rows by 16-byte
 // bulk copies, so their rows hold an even number of complex FP32 values (an
 // odd m gets one zero column, which every step leaves zero)
@@ -65,15 +103,32 @@ static void oras_apply_impl(const FrontsDev& F, const C* ws, const In* x, Out* y
                             cudaStream_t st, const SweepCfg& sc) {
     const int th = 256;
     const int ld = sizeof(C) == sizeof(float2) ? sweep_ld(m, sc.tc) : m;
-    int64_t tot = F.nloc * ld;
-    gather_kernel<In, C><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(F.nloc, m, ld, F.loc2glob.p, x, Y);
+    // complex FP32 throughout with even m and ld: 16-byte accesses
+    constexpr bool c64 = std::is_same<C, float2>::value && std::is_same<In, float2>::value &&
+                         std::is_same<Out, float2>::value;
+    const bool pairs = c64 && (m % 2) == 0 && (ld % 2) == 0;
+    const int64_t n = (int64_t)F.own_ptr.n - 1;
+    if (pairs) {
+        const dim3 b = pair_block(m / 2);
+        gather2_kernel<<<(unsigned)((F.nloc + b.y - 1) / b.y), b, 0, st>>>(
+            F.nloc, m / 2, ld / 2, F.loc2glob.p, reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(Y));
+    } else {
+        const int64_t tot = F.nloc * ld;
+        gather_kernel<In, C><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(F.nloc, m, ld, F.loc2glob.p, x, Y);
+    }
     MWI_CHECK_LAUNCH();
     multifrontal_solve<C>(F, ws, Y, Z, upd, ld, sc, st);
     // scatter into the global vector (n = own_ptr size - 1)
-    const int64_t n = (int64_t)F.own_ptr.n - 1;
-    tot = n * m;
-    scatter_kernel<C, Out><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(n, m, ld, F.own_ptr.p, F.own_row.p,
-                                                                          F.own_w.p, Y, y);
+    if (pairs) {
+        const dim3 b = pair_block(m / 2);
+        scatter2_kernel<<<(unsigned)((n + b.y - 1) / b.y), b, 0, st>>>(
+            n, m / 2, ld / 2, F.own_ptr.p, F.own_row.p, F.own_w.p, reinterpret_cast<const float4*>(Y),
+            reinterpret_cast<float4*>(y));
+    } else {
+        const int64_t tot = n * m;
+        scatter_kernel<C, Out><<<(unsigned)((tot + th - 1) / th), th, 0, st>>>(n, m, ld, F.own_ptr.p, F.own_row.p,
+                                                                              F.own_w.p, Y, y);
+    }
     MWI_CHECK_LAUNCH();
 }
 

@@ -531,9 +531,13 @@ void multifrontal_solve(const FrontsDev& F, const C* ws, C* Y, C* Z, C* upd, int
         if (tc5) launch_tc_product<C>(F, l, false, ws, Y, Z, upd, m, sc, st);
         else launch_gemm<C, kFwd>(F, l, ws, Y, Z, upd, m, tc, st);
     }
+    // backward levels of small fronts (mean pivot count below 40): the TF32
+    // mma.sync kernel with 32-row tiles beats the 128-row tcgen05 tiles there
+    // (one tile per front either way; the per-tile pipeline set-up of the
+    // tcgen05 kernel dominates), so the tcgen05 engine hands those levels to it
     for (int l = nlev - 1; l >= 0; --l) {
-        if (tc5) launch_tc_product<C>(F, l, true, ws, Y, Z, upd, m, sc, st);
-        else launch_gemm<C, kBwd>(F, l, ws, Y, Z, upd, m, tc, st);
+        if (tc5 && !small_tiles<C>(F, l, false)) launch_tc_product<C>(F, l, true, ws, Y, Z, upd, m, sc, st);
+        else launch_gemm<C, kBwd>(F, l, ws, Y, Z, upd, m, tc5 ? 2 : tc, st);
     }
 }
 
