@@ -33,10 +33,11 @@
 //
 // Kernel: persistent, two CTAs per SM, tiles (front, 128-row tile, 32-column
 // chunk) taken in a fixed stride.  Warp roles:
-//   warp 0      bulk copies: lane 0 the panel blocks, every lane one
-//               right-hand-side row (256 B) into the stage's staging rows
-//               (the update-row indices of the backward product looked up
-//               by the lanes first), one mbarrier transaction count
+//   warp 0      bulk copies: lanes 0-3 the panel blocks, the right-hand-side
+//               rows into the stage's staging rows (one copy per run of
+//               rows that are contiguous in memory, else one per row; the
+//               update-row indices of the backward product looked up by
+//               the lanes first), one mbarrier transaction count
 //   warp 1      owns the tensor memory (2 x 128 columns: accumulators double
 //               buffered across tiles); one lane issues tcgen05.mma and commits
 //   warps 2-3   transpose the staging rows into the K-major B tile (shared
@@ -67,7 +68,7 @@ constexpr int kUrCache = 1024;              // update-row indices of a backward 
 constexpr int kKS = 4;                      // K chunks of 8 per stage (K = 32)
 constexpr int kAStage = 32768;              // 4 K chunks x 16 groups of 8 M lines x 2 planes x 256 B
 constexpr int kBStage = 8192;               // 64 real columns x 32 K floats
-constexpr int kStage = kAStage + 2 * kBStage;  // + the staging rows [32][32 complex] of the copies
+constexpr int kStage = kAStage + 2 * kBStage;  // + the staging rows [32][nc complex] of the copies
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;
 constexpr int kSmemBytes = kStages * kStage + 1024 /* barriers */ + kUrCache * 4 + 1024 /* alignment */;
@@ -307,7 +308,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sweep_tc_kernel(
                 if (lane < nk)
                     bulk_g2s(a_dst + lane * 8192, P + ((int64_t)(k0 + lane) * G.cstride + G.g0) * 128, a_bytes,
                              raw_bar(s));
-                if (lane < nv) bulk_g2s(a_dst + kAStage + kBStage + lane * 256, src, row_bytes, raw_bar(s));
+                // right-hand-side rows: with one column chunk (nc = m) consecutive rows are
+                // contiguous in memory, so each run of consecutive source rows moves as one
+                // copy (the forward pivot rows are one run; the backward rows a few)
+                const unsigned long long sa = reinterpret_cast<unsigned long long>(src);
+                const unsigned long long prev = __shfl_up_sync(0xffffffffu, sa, 1);
+                const bool lead = lane < nv && (nchunks > 1 || lane == 0 || sa != prev + row_bytes);
+                const unsigned leaders = __ballot_sync(0xffffffffu, lead);
+                if (lead) {
+                    const unsigned later = leaders & ~((2u << lane) - 1u);
+                    const int len = (later ? __ffs(later) - 1 : nv) - lane;
+                    bulk_g2s(a_dst + kAStage + kBStage + lane * row_bytes, src, row_bytes * (uint32_t)len, raw_bar(s));
+                }
             }
         }
     } else if (warp == 1) {
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sweep_tc_kernel(
             }
         }
     } else if (warp < 4) {
-        // ---------------- staging rows [32][32 complex] -> K-major B tile
+        // ---------------- staging rows [32][nc complex] -> K-major B tile
         // (line = real column, 32 K floats, 128-byte swizzle); thread: column
         // `lane`, four groups of 4 rows
         const int rg = warp - 2;
@@ -354,7 +366,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sweep_tc_kernel(
         for (int ti = blockIdx.x; ti < total && ok; ti += gridDim.x) {
             const TileDesc d = tiles[ti / nchunks];
             const TcGeom G = tc_geom<MODE>(d);
-            const bool cin = (ti % nchunks) * 32 + lane < m;
+            const int nc = min(32, m - (ti % nchunks) * 32);  // columns of the chunk (staging row length)
+            const bool cin = lane < nc;
             for (int st = 0; st < G.nst; ++st, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
@@ -369,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sweep_tc_kernel(
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int r = 4 * q + j;
-                        v[j] = (cin && r < nv) ? R[r * 32 + lane] : make_float2(0.f, 0.f);
+                        v[j] = (cin && r < nv) ? R[r * nc + lane] : make_float2(0.f, 0.f);
                     }
                     const int n0 = 2 * lane;
                     *reinterpret_cast<float4*>(B + (n0 >> 3) * 1024 + (n0 & 7) * 128 + ((q ^ (n0 & 7)) << 4)) =
