@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--nz", type=int, default=42)
     ap.add_argument("--n-ant", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nd-leaf", type=int, default=64)
+    ap.add_argument("--nd-leaf", type=int, default=128)
     ap.add_argument("--clocks-csv", default=None, help="directory for the nvidia-smi clock samples (CSV)")
     ap.add_argument("--serve", type=int, default=0,
                     help="run the serving scenario with this many Poisson requests instead of the gradient step")
@@ -736,7 +736,7 @@ def run_solve(args):
     M = mwi.Mesh(mesh.xyz, mesh.tet, mesh.bface_tag, order=order)
     t1 = time.time()
     P = mwi.Problem(M, eps, FREQ, n_sub=n_sub, precision=prec, rtol=RTOL, max_block=max_block, restart=restart,
-                    sweep_engine=args.engine, verbose=2)
+                    sweep_engine=args.engine, nd_leaf=args.nd_leaf, verbose=2)
     coarse = None
     if args.coarse:
         cxy, cz = [int(v) for v in args.coarse.split(",")]
@@ -753,7 +753,7 @@ def run_solve(args):
     kms, kcnt = P.kernel_times(reset=True)
     info = P.info.as_dict()
     line = {"mode": "solve", "tets": int(mesh.nt), "dof": int(M.ndof), "order": order, "columns": int(ants.shape[0]),
-            "n_sub": n_sub, "precision": prec, "engine": args.engine, "mesh_s": round(t1 - t0, 2),
+            "n_sub": n_sub, "precision": prec, "engine": args.engine, "nd_leaf": args.nd_leaf, "mesh_s": round(t1 - t0, 2),
             "setup_s": round(t2 - t1, 2), "forward_s": round(t3 - t2, 3),
             "rhs_solves_per_s": round(ants.shape[0] / (t3 - t2), 2), "factor": P.factor_stats(),
             "oras_impl_bytes_per_call": P.oras_traffic(min(32, ants.shape[0])), "solve": info,

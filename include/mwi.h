@@ -86,7 +86,7 @@ typedef struct {
                                  preconditioner of the FP64 FGMRES [0] */
     int32_t inner_iters;  /* MIXED_NESTED: inner GMRES iterations per outer step [30] */
     double inner_rtol;    /* MIXED_NESTED: inner relative residual target [1e-4] */
-    int32_t nd_leaf;      /* nested-dissection leaf size of the subdomain ordering [64] */
+    int32_t nd_leaf;      /* nested-dissection leaf size of the subdomain ordering [128] */
     int32_t verbose;      /* 0 silent, 1 phase timings on stderr [0] */
     const int32_t* part;  /* optional [nt] host array: caller's tet -> subdomain map
                              (values in [0, n_sub)); NULL = recursive coordinate bisection */

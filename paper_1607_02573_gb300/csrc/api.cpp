@@ -253,7 +253,7 @@ mwi_solver_opts defaults(const mwi_solver_opts* o) {
     else if (d.overlap < 0) d.overlap = 0;
     if (d.inner_iters <= 0) d.inner_iters = 30;
     if (d.inner_rtol <= 0) d.inner_rtol = 1e-4;
-    if (d.nd_leaf <= 0) d.nd_leaf = 64;
+    if (d.nd_leaf <= 0) d.nd_leaf = 128;
     if (d.max_block <= 0) d.max_block = 64;
     if (d.sweep_engine <= 0) d.sweep_engine = 4;
     if (d.block_krylov < 0 || d.block_krylov > 1) throw Error(MWI_EINVAL, "block_krylov must be 0 or 1");
