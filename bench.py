@@ -368,9 +368,10 @@ def run_mine(args, rank, world):
 
 
 # DRAM bytes of one ORAS apply of the bench workload, summed over its launches
-# from ncu's dram__bytes_read.sum + dram__bytes_write.sum; None until the
-# counters are taken again for the current kernels
-ORAS_TRAFFIC = None
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum (tcgen05 sweeps,
+# nested-dissection leaf 128)
+ORAS_TRAFFIC = {"bytes_per_call": 8.036e9,
+                "source": "ncu DRAM counters of one apply at the bench size, profiles/oras_apply_chamber402k_traffic.md"}
 
 
 def db_bins(S, S_ref, edges=(0.0, -20.0, -60.0)):
