@@ -279,7 +279,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) sweep_tc_kernel(
             const bool ur_cached = MODE == kBwdT && u <= kUrCache;
             __syncwarp();
             if (ur_cached) {
-                for (int j = lane; j < u; j += 32) sur[j] = ur[j];
+                // eight loads in flight per lane before their stores
+                for (int j0 = 0; j0 < u; j0 += 256) {
+                    int v[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int j = j0 + 32 * t + lane;
+                        v[t] = j < u ? ur[j] : 0;
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int j = j0 + 32 * t + lane;
+                        if (j < u) sur[j] = v[t];
+                    }
+                }
                 __syncwarp();
             }
             for (int st = 0; st < G.nst; ++st, ++g) {
