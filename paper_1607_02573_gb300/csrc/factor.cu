@@ -215,8 +215,13 @@ __global__ void __launch_bounds__(256) update_kernel(const int4* __restrict__ ti
     if ((int64_t)bi * TILE >= nrem) return;
     C* F = ws + f_off[s];
     constexpr int MT = TILE / 16;
-    __shared__ C As[NB][TILE + 1];
-    __shared__ C Bs[NB][TILE + 1];
+    // complex FP32: a thread's rows (and columns) are the pairs 2t, 2t + 1 and
+    // 32 + 2t, 32 + 2t + 1, read as 16-byte shared loads (rows padded to an even
+    // length so that every pair is 16-byte aligned)
+    constexpr bool kPairs = sizeof(C) == sizeof(float2) && MT == 4;
+    constexpr int LD = kPairs ? TILE + 2 : TILE + 1;
+    __shared__ __align__(16) C As[NB][LD];
+    __shared__ __align__(16) C Bs[NB][LD];
     const int tid = threadIdx.x;
     const int64_t rowA = r0 + (int64_t)bi * TILE, rowB = r0 + (int64_t)bj * TILE;
     for (int e = tid; e < NB * TILE; e += 256) {
@@ -232,6 +237,8 @@ __global__ void __launch_bounds__(256) update_kernel(const int4* __restrict__ ti
     }
     __syncthreads();
     const int tx = tid % 16, ty = tid / 16;
+    // local row of accumulator a (column of b) within the tile
+    auto off = [](int t, int a) { return kPairs ? 32 * (a >> 1) + 2 * t + (a & 1) : t + 16 * a; };
     C acc[MT][MT];
 #pragma unroll
     for (int a = 0; a < MT; ++a)
@@ -240,10 +247,22 @@ __global__ void __launch_bounds__(256) update_kernel(const int4* __restrict__ ti
 #pragma unroll 4
     for (int j = 0; j < NB; ++j) {
         C av[MT], bv[MT];
+        if constexpr (kPairs) {
 #pragma unroll
-        for (int a = 0; a < MT; ++a) av[a] = As[j][tx + 16 * a];
+            for (int h = 0; h < 2; ++h) {
+                const float4 pa = *reinterpret_cast<const float4*>(&As[j][32 * h + 2 * tx]);
+                const float4 pb = *reinterpret_cast<const float4*>(&Bs[j][32 * h + 2 * ty]);
+                av[2 * h] = cmake<C>(pa.x, pa.y);
+                av[2 * h + 1] = cmake<C>(pa.z, pa.w);
+                bv[2 * h] = cmake<C>(pb.x, pb.y);
+                bv[2 * h + 1] = cmake<C>(pb.z, pb.w);
+            }
+        } else {
 #pragma unroll
-        for (int b = 0; b < MT; ++b) bv[b] = Bs[j][ty + 16 * b];
+            for (int a = 0; a < MT; ++a) av[a] = As[j][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < MT; ++b) bv[b] = Bs[j][ty + 16 * b];
+        }
 #pragma unroll
         for (int a = 0; a < MT; ++a)
 #pragma unroll
@@ -253,13 +272,13 @@ __global__ void __launch_bounds__(256) update_kernel(const int4* __restrict__ ti
     C* S = sch + sch_off[s];
 #pragma unroll
     for (int b = 0; b < MT; ++b) {
-        const int64_t col = rowB + ty + 16 * b;
+        const int64_t col = rowB + off(ty, b);
         if (col >= f) continue;
         // pivot columns live in the panel (ld f), the others in the Schur block (ld u)
         C* colp = col < p ? F + col * f : S + (col - p) * u - p;
 #pragma unroll
         for (int a = 0; a < MT; ++a) {
-            const int64_t row = rowA + tx + 16 * a;
+            const int64_t row = rowA + off(tx, a);
             if (row < f && row >= col) {
                 C& dst = colp[row];
                 dst = csub(dst, acc[a][b]);
