@@ -103,9 +103,19 @@ __global__ void __launch_bounds__(128) panel_diag_kernel(const int32_t* __restri
     const int nb = min(NB, p - k);
     C* F = ws + f_off[s];
     C (*Dg)[NB + 1] = Dgs[warp];
-    for (int e = lane; e < NB * NB; e += 32) {
-        const int r = e % NB, c = e / NB;
-        Dg[r][c] = (r < nb && c < nb && r >= c) ? F[(int64_t)(k + c) * f + k + r] : czero<C>();
+    {
+        // every load of the lane in flight before the stores
+        C v[NB * NB / 32];
+#pragma unroll
+        for (int t = 0; t < NB * NB / 32; ++t) {
+            const int e = lane + 32 * t, r = e % NB, c = e / NB;
+            v[t] = (r < nb && c < nb && r >= c) ? F[(int64_t)(k + c) * f + k + r] : czero<C>();
+        }
+#pragma unroll
+        for (int t = 0; t < NB * NB / 32; ++t) {
+            const int e = lane + 32 * t;
+            Dg[e % NB][e / NB] = v[t];
+        }
     }
     __syncwarp();
     const int r = lane;
@@ -164,14 +174,19 @@ __global__ void __launch_bounds__(128) panel_rows_kernel(const int2* __restrict_
     const int64_t f = (int64_t)p + U[s];
     const int nb = min(NB, p - k);
     C* F = ws + f_off[s];
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        C v = czero<C>();
-        if (r < nb && c < nb && r <= c) {
-            const C x = F[(int64_t)(k + c) * f + k + r];
-            v = r == c ? crecip(x) : x;
+    {
+        // the block's loads in flight before the stores (128 threads)
+        C v[NB * NB / 128];
+#pragma unroll
+        for (int t = 0; t < NB * NB / 128; ++t) {
+            const int e = threadIdx.x + 128 * t, r = e % NB, c = e / NB;
+            v[t] = (r < nb && c < nb && r <= c) ? F[(int64_t)(k + c) * f + k + r] : czero<C>();
         }
-        M[r][c] = v;
+#pragma unroll
+        for (int t = 0; t < NB * NB / 128; ++t) {
+            const int e = threadIdx.x + 128 * t, r = e % NB, c = e / NB;
+            M[r][c] = r == c && r < nb ? crecip(v[t]) : v[t];
+        }
     }
     __syncthreads();
     const int64_t i = (int64_t)tl.y + threadIdx.x;
@@ -199,7 +214,7 @@ __global__ void __launch_bounds__(128) panel_rows_kernel(const int2* __restrict_
 // rows/cols in [k + nb, f).  TILE x TILE output tile per block, 256 threads.
 // One block per tile (front, bi, bj >= ... bi) of the level's tile list for step k.
 template <typename C, int TILE, int NB>
-__global__ void __launch_bounds__(256) update_kernel(const int4* __restrict__ tiles, int k,
+__global__ void __launch_bounds__(256, 4) update_kernel(const int4* __restrict__ tiles, int k,
                                                      const int32_t* __restrict__ P, const int32_t* __restrict__ U,
                                                      const int64_t* __restrict__ f_off,
                                                      const int64_t* __restrict__ sch_off, C* __restrict__ ws,
@@ -224,16 +239,26 @@ __global__ void __launch_bounds__(256) update_kernel(const int4* __restrict__ ti
     __shared__ __align__(16) C Bs[NB][LD];
     const int tid = threadIdx.x;
     const int64_t rowA = r0 + (int64_t)bi * TILE, rowB = r0 + (int64_t)bj * TILE;
-    for (int e = tid; e < NB * TILE; e += 256) {
-        int ii = e % TILE, j = e / TILE;
-        C a = czero<C>(), b = czero<C>();
-        if (j < nb) {
-            C d = F[(int64_t)(k + j) * f + k + j];
-            if (rowA + ii < f) a = cmul(F[(int64_t)(k + j) * f + rowA + ii], d);
-            if (rowB + ii < f) b = F[(int64_t)(k + j) * f + rowB + ii];
+    {
+        // every load of the thread in flight before the products and stores
+        constexpr int NT = NB * TILE / 256;
+        C av[NT], bv[NT], dv[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int e = tid + 256 * t, ii = e % TILE, j = e / TILE;
+            av[t] = bv[t] = dv[t] = czero<C>();
+            if (j < nb) {
+                dv[t] = F[(int64_t)(k + j) * f + k + j];
+                if (rowA + ii < f) av[t] = F[(int64_t)(k + j) * f + rowA + ii];
+                if (rowB + ii < f) bv[t] = F[(int64_t)(k + j) * f + rowB + ii];
+            }
         }
-        As[j][ii] = a;
-        Bs[j][ii] = b;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int e = tid + 256 * t, ii = e % TILE, j = e / TILE;
+            As[j][ii] = cmul(av[t], dv[t]);
+            Bs[j][ii] = bv[t];
+        }
     }
     __syncthreads();
     const int tx = tid % 16, ty = tid / 16;
@@ -382,8 +407,20 @@ __global__ void copy_inverse_kernel(const int32_t* __restrict__ level_fronts, in
     const C* T = tmp + inv_off[lo + blockIdx.y] + (int64_t)j * f;
     const C d = L[j];
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < f; i += blockDim.x)
-        L[i] = i > j ? T[i] : (i == j ? cmake<C>(1, 0) : czero<C>());
+    // four loads per thread in flight before their stores
+    for (int64_t i0 = 0; i0 < f; i0 += 4 * (int64_t)blockDim.x) {
+        C v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t i = i0 + t * (int64_t)blockDim.x + threadIdx.x;
+            v[t] = (i < f && i > j) ? T[i] : (i == j ? cmake<C>(1, 0) : czero<C>());
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t i = i0 + t * (int64_t)blockDim.x + threadIdx.x;
+            if (i < f) L[i] = v[t];
+        }
+    }
     if (threadIdx.x == 0) dinv[sub_off[sub[s]] + start[s] + j] = crecip(d);
 }
 
