@@ -117,6 +117,7 @@ struct mwi_mesh {
     int refcount = 0;
     cudaStream_t st = nullptr;  // internal stream for setup work
     DevBuf<double> xyz, Kp, Mp, Bf;
+    DevBuf<float2> Mdf;  // element masses as double-float pairs (first order, built on first use)
     DevBuf<int32_t> tv, tet_dofs, face_dofs, tet_faces, face_tets;
     DevBuf<int8_t> face_lf, face_tag;
     ElementTablesDev tabs;
@@ -1466,8 +1467,27 @@ static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const 
             out = P->grad_d.p;
         }
         mwi_mesh* M = P->mesh;
-        launch_gradient(T.order, T.nt, P->m_fwd, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p, M->face_dofs.p,
-                        M->Mp.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, out, st);
+        if (P->opts.precision != 0 && T.order == 1) {
+            // mixed: the volume term in double-float (U and Lam split into the
+            // solver's double-float scratch planes, free after the adjoint solve)
+            const int64_t nm = T.ndof * (int64_t)P->m_fwd;
+            {
+                std::lock_guard<std::mutex> lk(M->mu);
+                if (!M->Mdf.p) {
+                    M->Mdf.alloc((size_t)T.nt * 21);
+                    launch_split_real(T.nt * 21, M->Mp.p, M->Mdf.p, st);
+                }
+            }
+            P->Xdf.ensure(2 * (size_t)nm);
+            P->Rdf.ensure(2 * (size_t)nm);
+            split_c128(nm, P->U.p, P->Xdf.p, st);
+            split_c128(nm, P->Lam.p, P->Rdf.p, st);
+            launch_gradient_df(T.nt, P->m_fwd, nm, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p, M->face_dofs.p,
+                               M->Mdf.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, P->Xdf.p, P->Rdf.p, out, st);
+        } else {
+            launch_gradient(T.order, T.nt, P->m_fwd, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p, M->face_dofs.p,
+                            M->Mp.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, out, st);
+        }
         MWI_CUDA(cudaMemcpyAsync(J_out, P->J_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         if (!dev)
             MWI_CUDA(cudaMemcpyAsync(dJ, P->grad_d.p, T.nt * sizeof(double2), cudaMemcpyDeviceToHost, st));

@@ -12,6 +12,7 @@
 //     G_t = sum_j lam_{j,t}^T (k0^2 M_t - i k0 / (2 sqrt(eps_t)) B_t) u_{j,t},
 //     dJ/dRe(eps_t) + i dJ/dIm(eps_t) = conj(G_t).
 #include "common.h"
+#include "df.h"
 #include "physics.h"
 
 namespace mwi {
@@ -169,7 +170,158 @@ __global__ void __launch_bounds__(256) gradient_kernel(
     }
 }
 
+// The same gradient for the mixed path and first order with the volume term in
+// double-float arithmetic on the FP32 pipes (FP64 runs at 1/64 of the FP32
+// rate, and the FP64 form of this kernel is bound by it): U and Lam as
+// double-float planes (hi at [0, nm), lo at [nm, 2 nm), complex pairs), the
+// element masses as double-float pairs Mdf [nt][21] (split once per mesh), the
+// sums over the transmitters and across the warp in double-float, one join to
+// FP64 per tet.  The boundary term (impedance faces only) stays in FP64.
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    dfl r;
+    quick_two_sum(s, e + (a.l + b.l), r.h, r.l);
+    return r;
+}
+
+__global__ void __launch_bounds__(256, 2) gradient_df_kernel(
+    int64_t nt, int m, int64_t nm, const int32_t* __restrict__ tet_dofs, const int32_t* __restrict__ tet_faces,
+    const int8_t* __restrict__ face_tag, const int32_t* __restrict__ face_dofs, const float2* __restrict__ Mdf,
+    const double* __restrict__ Bf, const double2* __restrict__ eps, double k0, const double2* __restrict__ U,
+    const double2* __restrict__ Lam, const float2* __restrict__ Udf, const float2* __restrict__ Ldf,
+    double2* __restrict__ out) {
+    constexpr int NL = 6, NLF = 3, NP = 21, NPF = 6;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nt) return;
+    int dofs[NL];
+#pragma unroll
+    for (int a = 0; a < NL; ++a) dofs[a] = tet_dofs[t * NL + a];
+    int ff[4], nff = 0;
+#pragma unroll
+    for (int lf = 0; lf < 4; ++lf) {
+        const int f = tet_faces[t * 4 + lf];
+        if (face_tag[f] == 2) ff[nff++] = f;
+    }
+    const float2* Mt = Mdf + t * NP;
+    dfl vr = {0.f, 0.f}, vi = {0.f, 0.f};  // volume sum
+    double br = 0.0, bi = 0.0;             // boundary sum
+    for (int c = lane; c < m; c += 32) {
+        float2 uh[NL], ul[NL], lh[NL], ll[NL];
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+            uh[a] = ul[a] = lh[a] = ll[a] = make_float2(0.f, 0.f);
+            if (dofs[a] >= 0) {
+                const int64_t e = (int64_t)dofs[a] * m + c;
+                uh[a] = Udf[e];
+                ul[a] = Udf[nm + e];
+                lh[a] = Ldf[e];
+                ll[a] = Ldf[nm + e];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+            dfl mr = {0.f, 0.f}, mi = {0.f, 0.f};  // (M u)_a
+#pragma unroll
+            for (int b = 0; b < NL; ++b) {
+                const int ia = a < b ? a : b, ib = a < b ? b : a;
+                const float2 mab = Mt[ia * NL - ia * (ia - 1) / 2 + (ib - ia)];
+                df_mac(mr, mab.x, mab.y, uh[b].x, ul[b].x);
+                df_mac(mi, mab.x, mab.y, uh[b].y, ul[b].y);
+            }
+            mr = df_norm(mr);
+            mi = df_norm(mi);
+            // v += lam_a (M u)_a
+            df_mac(vr, lh[a].x, ll[a].x, mr.h, mr.l);
+            df_mac(vr, -lh[a].y, -ll[a].y, mi.h, mi.l);
+            df_mac(vi, lh[a].x, ll[a].x, mi.h, mi.l);
+            df_mac(vi, lh[a].y, ll[a].y, mr.h, mr.l);
+        }
+        for (int q = 0; q < nff; ++q) {
+            const int f = ff[q];
+            double2 uf[NLF], lf_[NLF];
+#pragma unroll
+            for (int a = 0; a < NLF; ++a) {
+                const int d = face_dofs[(int64_t)f * NLF + a];
+                uf[a] = d >= 0 ? U[(int64_t)d * m + c] : make_double2(0.0, 0.0);
+                lf_[a] = d >= 0 ? Lam[(int64_t)d * m + c] : make_double2(0.0, 0.0);
+            }
+            const double* Bp = Bf + (int64_t)f * NPF;
+#pragma unroll
+            for (int a = 0; a < NLF; ++a) {
+                double2 bu = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int b = 0; b < NLF; ++b) {
+                    const int ia = a < b ? a : b, ib = a < b ? b : a;
+                    const double bab = Bp[ia * NLF - ia * (ia - 1) / 2 + (ib - ia)];
+                    bu.x += bab * uf[b].x;
+                    bu.y += bab * uf[b].y;
+                }
+                br += lf_[a].x * bu.x - lf_[a].y * bu.y;
+                bi += lf_[a].x * bu.y + lf_[a].y * bu.x;
+            }
+        }
+    }
+    vr = df_norm(vr);
+    vi = df_norm(vi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dfl xr, xi;
+        xr.h = __shfl_xor_sync(0xffffffffu, vr.h, o);
+        xr.l = __shfl_xor_sync(0xffffffffu, vr.l, o);
+        xi.h = __shfl_xor_sync(0xffffffffu, vi.h, o);
+        xi.l = __shfl_xor_sync(0xffffffffu, vi.l, o);
+        vr = df_add(vr, xr);
+        vi = df_add(vi, xi);
+    }
+    if (nff > 0) {  // the same for every lane of the warp (one tet)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            br += __shfl_xor_sync(0xffffffffu, br, o);
+            bi += __shfl_xor_sync(0xffffffffu, bi, o);
+        }
+    }
+    if (lane == 0) {
+        const double k2 = k0 * k0;
+        double gr = k2 * df_join(vr.h, vr.l), gi = k2 * df_join(vi.h, vi.l);
+        if (nff > 0) {
+            // coef = -i k0 / (2 sqrt(eps))
+            const double2 e = eps[t];
+            const double r = sqrt(e.x * e.x + e.y * e.y);
+            double sx = sqrt(0.5 * (r + e.x)), sy = sqrt(0.5 * (r - e.x));
+            if (e.y < 0) sy = -sy;
+            const double den = 2.0 * (sx * sx + sy * sy);
+            const double cr = -k0 * sy / den;
+            const double ci = -k0 * sx / den;
+            gr += cr * br - ci * bi;
+            gi += cr * bi + ci * br;
+        }
+        out[t] = make_double2(gr, -gi);
+    }
+}
+
+// double-float pairs of a real array
+__global__ void split_real_kernel(int64_t count, const double* __restrict__ a, float2* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < count) out[e] = df_split(a[e]);
+}
+
 static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+
+void launch_split_real(int64_t count, const double* a, float2* out, cudaStream_t st) {
+    split_real_kernel<<<nblk(count, 256), 256, 0, st>>>(count, a, out);
+    MWI_CHECK_LAUNCH();
+}
+
+void launch_gradient_df(int64_t nt, int m, int64_t nm, const int32_t* tet_dofs, const int32_t* tet_faces,
+                        const int8_t* face_tag, const int32_t* face_dofs, const float2* Mdf, const double* Bf,
+                        const double2* eps, double k0, const double2* U, const double2* Lam, const float2* Udf,
+                        const float2* Ldf, double2* out, cudaStream_t st) {
+    gradient_df_kernel<<<nblk(nt * 32, 256), 256, 0, st>>>(nt, m, nm, tet_dofs, tet_faces, face_tag, face_dofs, Mdf,
+                                                           Bf, eps, k0, U, Lam, Udf, Ldf, out);
+    MWI_CHECK_LAUNCH();
+}
 
 void launch_rhs(int m, const int32_t* dof, const double* sign, const double2* cur, double omega_mu0, double2* B,
                 cudaStream_t st) {
