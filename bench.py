@@ -370,7 +370,7 @@ def run_mine(args, rank, world):
 # DRAM bytes of one ORAS apply of the bench workload, summed over its launches
 # from ncu's dram__bytes_read.sum + dram__bytes_write.sum (tcgen05 sweeps,
 # nested-dissection leaf 128)
-ORAS_TRAFFIC = {"bytes_per_call": 8.036e9,
+ORAS_TRAFFIC = {"bytes_per_call": 8.034e9,
                 "source": "ncu DRAM counters of one apply at the bench size, profiles/oras_apply_chamber402k_traffic.md"}
 
 
