@@ -264,12 +264,9 @@ void coarse_values(const std::vector<int64_t>& A_rp, const std::vector<int32_t>&
     const int64_t nc = C.nc;
     out.assign(C.Ac_col.size(), make_double2(0.0, 0.0));
     parallel_for(nc, 16, [&](int64_t E, int) {
-        thread_local std::vector<double2> acc;
+        // position of each coarse column in row E (-1 elsewhere; reset after the row)
         thread_local std::vector<int32_t> pos;
-        if ((int64_t)acc.size() < nc) {
-            acc.assign(nc, make_double2(0.0, 0.0));
-            pos.assign(nc, -1);
-        }
+        if ((int64_t)pos.size() < nc) pos.assign(nc, -1);
         for (int64_t q = C.Ac_rp[E]; q < C.Ac_rp[E + 1]; ++q) pos[C.Ac_col[q]] = (int32_t)(q - C.Ac_rp[E]);
         const int64_t base = C.Ac_rp[E];
         for (int64_t q = C.PT_rp[E]; q < C.PT_rp[E + 1]; ++q) {
