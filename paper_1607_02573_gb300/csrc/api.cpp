@@ -1472,10 +1472,14 @@ static mwi_status misfit_grad_impl(mwi_problem_t P, const double* S_meas, const 
             // solver's double-float scratch planes, free after the adjoint solve)
             const int64_t nm = T.ndof * (int64_t)P->m_fwd;
             {
+                // built once per mesh on the mesh's stream and finished before any
+                // problem on the mesh (any stream) can see it
                 std::lock_guard<std::mutex> lk(M->mu);
                 if (!M->Mdf.p) {
-                    M->Mdf.alloc((size_t)T.nt * 21);
-                    launch_split_real(T.nt * 21, M->Mp.p, M->Mdf.p, st);
+                    DevBuf<float2> mdf((size_t)T.nt * 21);
+                    launch_split_real(T.nt * 21, M->Mp.p, mdf.p, M->st);
+                    MWI_CUDA(cudaStreamSynchronize(M->st));
+                    M->Mdf = std::move(mdf);
                 }
             }
             P->Xdf.ensure(2 * (size_t)nm);
