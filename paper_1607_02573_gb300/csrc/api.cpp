@@ -133,6 +133,7 @@ struct mwi_mesh {
     bool have_p1 = false;
     DevBuf<int32_t> v2t_ptr, v2t, p1_rp, p1_col;
     DevBuf<double> p1_val, Mv;
+    DevBuf<float2> Mvdf;  // Mv as double-float pairs (first order, built on first mixed use)
 };
 
 struct mwi_problem {
@@ -1707,9 +1708,33 @@ mwi_status mwi_misfit_and_gradient_kappa_device(mwi_problem_t P, const double* S
         const Topology& T = M->T;
         cudaStream_t st = P->st;
         P->grad_tw.ensure((size_t)T.nt * 4);
-        launch_p1_tet_gradient(T.order, T.nt, P->m_fwd, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p,
-                               M->face_dofs.p, M->Mv.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, P->grad_tw.p,
-                               st);
+        if (P->opts.precision != 0 && T.order == 1) {
+            // mixed: the volume terms in double-float (U and Lam split into the
+            // solver's double-float scratch planes, free after the adjoint solve)
+            const int64_t nm = T.ndof * (int64_t)P->m_fwd;
+            {
+                // built once per mesh on the mesh's stream and finished before any
+                // problem on the mesh (any stream) can see it
+                std::lock_guard<std::mutex> lk(M->mu);
+                if (!M->Mvdf.p) {
+                    DevBuf<float2> mv((size_t)T.nt * 4 * 21);
+                    launch_split_real(T.nt * 4 * 21, M->Mv.p, mv.p, M->st);
+                    MWI_CUDA(cudaStreamSynchronize(M->st));
+                    M->Mvdf = std::move(mv);
+                }
+            }
+            P->Xdf.ensure(2 * (size_t)nm);
+            P->Rdf.ensure(2 * (size_t)nm);
+            split_c128(nm, P->U.p, P->Xdf.p, st);
+            split_c128(nm, P->Lam.p, P->Rdf.p, st);
+            launch_p1_tet_gradient_df(T.nt, P->m_fwd, nm, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p,
+                                      M->face_dofs.p, M->Mvdf.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p,
+                                      P->Xdf.p, P->Rdf.p, P->grad_tw.p, st);
+        } else {
+            launch_p1_tet_gradient(T.order, T.nt, P->m_fwd, M->tet_dofs.p, M->tet_faces.p, M->face_tag.p,
+                                   M->face_dofs.p, M->Mv.p, M->Bf.p, P->eps.p, P->k0, P->U.p, P->Lam.p, P->grad_tw.p,
+                                   st);
+        }
         const int nb = p1_gradient_blocks(T.nv);
         P->p1_partial.ensure(nb);
         P->p1_partial_host.resize(nb);

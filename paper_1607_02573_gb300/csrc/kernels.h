@@ -217,6 +217,13 @@ void launch_p1_tet_gradient(int order, int64_t nt, int m, const int32_t* tet_dof
                             const int8_t* face_tag, const int32_t* face_dofs, const double* Mv, const double* Bf,
                             const double2* eps, double k0, const double2* U, const double2* Lam, double2* out_tw,
                             cudaStream_t st);
+// the same for the mixed path and first order, the volume terms in double-float:
+// U and Lam as double-float planes ([2][nm] complex pairs), Mvdf the vertex
+// masses as double-float pairs [nt][4][21]
+void launch_p1_tet_gradient_df(int64_t nt, int m, int64_t nm, const int32_t* tet_dofs, const int32_t* tet_faces,
+                               const int8_t* face_tag, const int32_t* face_dofs, const float2* Mvdf,
+                               const double* Bf, const double2* eps, double k0, const double2* U, const double2* Lam,
+                               const float2* Udf, const float2* Ldf, double2* out_tw, cudaStream_t st);
 int p1_gradient_blocks(int64_t nv);
 // per vertex: the (tet, vertex) gradients of its tets plus alpha K kappa;
 // partial[block] = the block's sum of Re(conj(kappa_v) (K kappa)_v)

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "df.h"
 #include "kernels.h"
 #include "model.h"
 
@@ -287,6 +288,166 @@ void launch_p1_mass(int64_t nt, int npack, const int32_t* tv, const double2* kap
                     cudaStream_t st) {
     const int64_t n = nt * npack;
     p1_mass_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nt, npack, tv, kappa, Mv, Mk);
+    MWI_CHECK_LAUNCH();
+}
+
+// The same (tet, vertex) gradient terms for the mixed path and first order
+// with the volume terms in double-float on the FP32 pipes (the FP64 form is
+// bound by the FP64 rate): U and Lam as double-float planes ([2][nm] complex
+// pairs), the vertex-weighted masses as double-float pairs Mvdf [nt][4][21]
+// (split once per mesh), one join to FP64 per (tet, vertex).  The boundary term
+// stays in FP64.
+__device__ __forceinline__ dfl p1_df_add(dfl a, dfl b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    dfl r;
+    quick_two_sum(s, e + (a.l + b.l), r.h, r.l);
+    return r;
+}
+
+__global__ void __launch_bounds__(256) p1_tet_gradient_df_kernel(
+    int64_t nt, int m, int64_t nm, const int32_t* __restrict__ tet_dofs, const int32_t* __restrict__ tet_faces,
+    const int8_t* __restrict__ face_tag, const int32_t* __restrict__ face_dofs, const float2* __restrict__ Mvdf,
+    const double* __restrict__ Bf, const double2* __restrict__ eps, double k0, const double2* __restrict__ U,
+    const double2* __restrict__ Lam, const float2* __restrict__ Udf, const float2* __restrict__ Ldf,
+    double2* __restrict__ out) {
+    constexpr int NL = 6, NLF = 3, NP = 21, NPF = 6;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= nt) return;
+    int dofs[NL];
+#pragma unroll
+    for (int a = 0; a < NL; ++a) dofs[a] = tet_dofs[t * NL + a];
+    const float2* Mt = Mvdf + t * 4 * NP;
+    int ff[4], nff = 0;
+#pragma unroll
+    for (int lf = 0; lf < 4; ++lf) {
+        const int f = tet_faces[t * 4 + lf];
+        if (face_tag[f] == 2) ff[nff++] = f;
+    }
+    dfl vr[4], vi[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) vr[w] = vi[w] = dfl{0.f, 0.f};
+    double br = 0.0, bi = 0.0;
+    for (int c = lane; c < m; c += 32) {
+        float2 uh[NL], ul[NL], lh[NL], ll[NL];
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+            uh[a] = ul[a] = lh[a] = ll[a] = make_float2(0.f, 0.f);
+            if (dofs[a] >= 0) {
+                const int64_t e = (int64_t)dofs[a] * m + c;
+                uh[a] = Udf[e];
+                ul[a] = Udf[nm + e];
+                lh[a] = Ldf[e];
+                ll[a] = Ldf[nm + e];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+            // (M^(w) u)_a for the four vertices w, then lam_a times each
+            dfl mr[4], mi[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) mr[w] = mi[w] = dfl{0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < NL; ++b) {
+                const int ia = a < b ? a : b, ib = a < b ? b : a;
+                const int q = ia * NL - ia * (ia - 1) / 2 + (ib - ia);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float2 mab = Mt[w * NP + q];
+                    df_mac(mr[w], mab.x, mab.y, uh[b].x, ul[b].x);
+                    df_mac(mi[w], mab.x, mab.y, uh[b].y, ul[b].y);
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const dfl r = df_norm(mr[w]), i = df_norm(mi[w]);
+                df_mac(vr[w], lh[a].x, ll[a].x, r.h, r.l);
+                df_mac(vr[w], -lh[a].y, -ll[a].y, i.h, i.l);
+                df_mac(vi[w], lh[a].x, ll[a].x, i.h, i.l);
+                df_mac(vi[w], lh[a].y, ll[a].y, r.h, r.l);
+            }
+        }
+        for (int q = 0; q < nff; ++q) {
+            const int f = ff[q];
+            double2 uf[NLF], lf_[NLF];
+#pragma unroll
+            for (int a = 0; a < NLF; ++a) {
+                const int d = face_dofs[(int64_t)f * NLF + a];
+                uf[a] = d >= 0 ? U[(int64_t)d * m + c] : make_double2(0.0, 0.0);
+                lf_[a] = d >= 0 ? Lam[(int64_t)d * m + c] : make_double2(0.0, 0.0);
+            }
+            const double* Bp = Bf + (int64_t)f * NPF;
+#pragma unroll
+            for (int a = 0; a < NLF; ++a) {
+                double2 bu = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int b = 0; b < NLF; ++b) {
+                    const int ia = a < b ? a : b, ib = a < b ? b : a;
+                    const double bab = Bp[ia * NLF - ia * (ia - 1) / 2 + (ib - ia)];
+                    bu.x += bab * uf[b].x;
+                    bu.y += bab * uf[b].y;
+                }
+                br += lf_[a].x * bu.x - lf_[a].y * bu.y;
+                bi += lf_[a].x * bu.y + lf_[a].y * bu.x;
+            }
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        vr[w] = df_norm(vr[w]);
+        vi[w] = df_norm(vi[w]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            dfl xr, xi;
+            xr.h = __shfl_xor_sync(0xffffffffu, vr[w].h, o);
+            xr.l = __shfl_xor_sync(0xffffffffu, vr[w].l, o);
+            xi.h = __shfl_xor_sync(0xffffffffu, vi[w].h, o);
+            xi.l = __shfl_xor_sync(0xffffffffu, vi[w].l, o);
+            vr[w] = p1_df_add(vr[w], xr);
+            vi[w] = p1_df_add(vi[w], xi);
+        }
+    }
+    if (nff > 0) {  // the same for every lane of the warp (one tet)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            br += __shfl_xor_sync(0xffffffffu, br, o);
+            bi += __shfl_xor_sync(0xffffffffu, bi, o);
+        }
+    }
+    if (lane == 0) {
+        // 1/4 of the beta term: coef = -i k0 / (2 sqrt(kappa_bar_t))
+        double qr = 0.0, qi = 0.0;
+        if (nff > 0) {
+            const double2 e = eps[t];
+            const double r = sqrt(e.x * e.x + e.y * e.y);
+            double sx = sqrt(0.5 * (r + e.x)), sy = sqrt(0.5 * (r - e.x));
+            if (e.y < 0) sy = -sy;
+            const double den = 2.0 * (sx * sx + sy * sy);
+            const double cr = -k0 * sy / den;
+            const double ci = -k0 * sx / den;
+            qr = 0.25 * (cr * br - ci * bi);
+            qi = 0.25 * (cr * bi + ci * br);
+        }
+        const double k2 = k0 * k0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            out[4 * t + w] = make_double2(k2 * df_join(vr[w].h, vr[w].l) + qr,
+                                          -(k2 * df_join(vi[w].h, vi[w].l) + qi));
+    }
+}
+
+void launch_p1_tet_gradient_df(int64_t nt, int m, int64_t nm, const int32_t* tet_dofs, const int32_t* tet_faces,
+                               const int8_t* face_tag, const int32_t* face_dofs, const float2* Mvdf,
+                               const double* Bf, const double2* eps, double k0, const double2* U, const double2* Lam,
+                               const float2* Udf, const float2* Ldf, double2* out_tw, cudaStream_t st) {
+    const int th = 256;
+    const unsigned blocks = (unsigned)((nt * 32 + th - 1) / th);
+    p1_tet_gradient_df_kernel<<<blocks, th, 0, st>>>(nt, m, nm, tet_dofs, tet_faces, face_tag, face_dofs, Mvdf, Bf,
+                                                     eps, k0, U, Lam, Udf, Ldf, out_tw);
     MWI_CHECK_LAUNCH();
 }
 
