@@ -389,6 +389,20 @@ mwi_status mwi_recycle_from(mwi_problem_t dst, mwi_problem_t src);
  * with a coarse space (MWI_EINVAL). */
 mwi_status mwi_set_coarse_space(mwi_problem_t prob, mwi_mesh_t coarse_mesh);
 
+/* Host-only form of the prolongation of mwi_set_coarse_space (no device
+ * work), for checking the host logic without a GPU: the fine mesh (order 1 or
+ * 2) and the coarse mesh (order 1) as mwi_mesh_create takes them; *n, *nc, *nnz
+ * the fine and coarse DOF counts and the entries of P; P in CSR (p_rp [n+1],
+ * p_col [nnz], p_val [nnz]) in the library's DOF numbering of each mesh, with
+ * the DOF keys of both numberings as mwi_mesh_dof_keys gives them (fkind [n],
+ * fverts [3n], ckind [nc], cverts [3nc]).  Call with null arrays to get the
+ * sizes; every array may be NULL. */
+mwi_status mwi_coarse_prolongation_host(const double* fxyz, int64_t fnv, const int32_t* ftet, int64_t fnt,
+                                        const int32_t* fbface_tag, int32_t forder, const double* cxyz, int64_t cnv,
+                                        const int32_t* ctet, int64_t cnt, const int32_t* cbface_tag, int64_t* n,
+                                        int64_t* nc, int64_t* nnz, int64_t* p_rp, int32_t* p_col, double* p_val,
+                                        int32_t* fkind, int64_t* fverts, int32_t* ckind, int64_t* cverts);
+
 /* Sizes of the problem's coarse space (all 0 without one): n_c coarse DOFs,
  * entries of P and of A_c, host+device setup time of the last (re)build of
  * A_c and its factors, and the factorisation's replaced pivots.  Any pointer

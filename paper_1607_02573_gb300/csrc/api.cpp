@@ -1898,6 +1898,31 @@ mwi_status mwi_set_coarse_space(mwi_problem_t P, mwi_mesh_t Mc) {
     });
 }
 
+mwi_status mwi_coarse_prolongation_host(const double* fxyz, int64_t fnv, const int32_t* ftet, int64_t fnt,
+                                        const int32_t* fbface_tag, int32_t forder, const double* cxyz, int64_t cnv,
+                                        const int32_t* ctet, int64_t cnt, const int32_t* cbface_tag, int64_t* n,
+                                        int64_t* nc, int64_t* nnz, int64_t* p_rp, int32_t* p_col, double* p_val,
+                                        int32_t* fkind, int64_t* fverts, int32_t* ckind, int64_t* cverts) {
+    return guard([&] {
+        MWI_REQUIRE(fxyz && ftet && fbface_tag && cxyz && ctet && cbface_tag, MWI_EINVAL, "null mesh array");
+        Topology Tf, Tc;
+        build_topology(Tf, fxyz, fnv, ftet, fnt, fbface_tag, forder);
+        build_topology(Tc, cxyz, cnv, ctet, cnt, cbface_tag, 1);
+        CoarseHost H;
+        build_prolongation(Tf, Tc, H);
+        if (n) *n = H.n;
+        if (nc) *nc = H.nc;
+        if (nnz) *nnz = (int64_t)H.P_col.size();
+        if (p_rp) std::copy(H.P_rp.begin(), H.P_rp.end(), p_rp);
+        if (p_col) std::copy(H.P_col.begin(), H.P_col.end(), p_col);
+        if (p_val) std::copy(H.P_val.begin(), H.P_val.end(), p_val);
+        if (fkind) std::copy(Tf.dof_kind.begin(), Tf.dof_kind.end(), fkind);
+        if (fverts) std::copy(Tf.dof_verts.begin(), Tf.dof_verts.end(), fverts);
+        if (ckind) std::copy(Tc.dof_kind.begin(), Tc.dof_kind.end(), ckind);
+        if (cverts) std::copy(Tc.dof_verts.begin(), Tc.dof_verts.end(), cverts);
+    });
+}
+
 mwi_status mwi_coarse_info(mwi_problem_t P, int64_t* n_coarse, int64_t* nnz_p, int64_t* nnz_ac, double* setup_ms,
                            int32_t* n_perturbed) {
     return guard([&] {

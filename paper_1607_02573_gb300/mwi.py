@@ -90,6 +90,9 @@ _SIGS = {
     "mwi_set_coarse_space": [_vp, _vp],
     "mwi_coarse_info": [_vp, _i64p, _i64p, _i64p, _dp, _i32p],
     "mwi_coarse_operator": [_vp, _i64p, _i32p, _dp, _i64p, _i32p, _dp],
+    "mwi_coarse_prolongation_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, _dp, C.c_int64, _i32p,
+                                     C.c_int64, _i32p, _i64p, _i64p, _i64p, _i64p, _i32p, _dp, _i32p, _i64p, _i32p,
+                                     _i64p],
 }
 EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
@@ -113,6 +116,37 @@ def check(status, allow=()):
     if status != MWI_OK and status not in allow:
         raise MwiError(status, (mwi_last_error() or b"").decode())
     return status
+
+
+def coarse_prolongation_host(fine, coarse, fine_order=1):
+    """The prolongation of the two-level ORAS between two meshes (objects with
+    xyz, tet, bface_tag, nv), computed on the host (mwi_coarse_prolongation_host):
+    (P as scipy CSR in the library's DOF numbering, (fine kind, fine verts),
+    (coarse kind, coarse verts))."""
+    import scipy.sparse as sp
+
+    def arrs(m):
+        return (np.ascontiguousarray(m.xyz, dtype=np.float64), np.ascontiguousarray(m.tet, dtype=np.int32),
+                np.ascontiguousarray(m.bface_tag, dtype=np.int32))
+
+    fx, ft, fb = arrs(fine)
+    cx, ct, cb = arrs(coarse)
+    n, nc, nnz = C.c_int64(), C.c_int64(), C.c_int64()
+    head = [_ptr(fx, C.c_double), fx.shape[0], _ptr(ft, C.c_int32), ft.shape[0], _ptr(fb, C.c_int32), fine_order,
+            _ptr(cx, C.c_double), cx.shape[0], _ptr(ct, C.c_int32), ct.shape[0], _ptr(cb, C.c_int32)]
+    check(mwi_coarse_prolongation_host(*head, C.byref(n), C.byref(nc), C.byref(nnz), None, None, None, None, None,
+                                       None, None))
+    rp = np.empty(n.value + 1, dtype=np.int64)
+    col = np.empty(nnz.value, dtype=np.int32)
+    val = np.empty(nnz.value, dtype=np.float64)
+    fk = np.empty(n.value, dtype=np.int32)
+    fv = np.empty((n.value, 3), dtype=np.int64)
+    ck = np.empty(nc.value, dtype=np.int32)
+    cv = np.empty((nc.value, 3), dtype=np.int64)
+    check(mwi_coarse_prolongation_host(*head, C.byref(n), C.byref(nc), C.byref(nnz), _ptr(rp, C.c_int64),
+                                       _ptr(col, C.c_int32), _ptr(val, C.c_double), _ptr(fk, C.c_int32),
+                                       _ptr(fv, C.c_int64), _ptr(ck, C.c_int32), _ptr(cv, C.c_int64)))
+    return sp.csr_matrix((val, col, rp), shape=(n.value, nc.value)), (fk, fv), (ck, cv)
 
 
 def normalised_weights(S_empty):
