@@ -179,6 +179,7 @@ struct mwi_problem {
     bool have_fwd = false, have_adj = false;
     std::vector<int32_t> rx_dof, tx_dof;
     std::vector<double> rx_sign, tx_sign;
+    std::vector<mwi_antenna> tx_key, rx_key;  // the antennas tx_dof / rx_dof (and their device copies) map
     DevBuf<int32_t> rx_dof_d, tx_dof_d;
     DevBuf<double> rx_sign_d, tx_sign_d;
     DevBuf<double2> cur_d, S_d, Smeas_d, r_d, grad_d;
@@ -885,6 +886,11 @@ void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<in
     }
 }
 
+// the same antennas, byte for byte, as the key
+bool same_antennas(const std::vector<mwi_antenna>& key, const mwi_antenna* a, int n) {
+    return (int64_t)key.size() == n && std::memcmp(key.data(), a, n * sizeof(mwi_antenna)) == 0;
+}
+
 // solve A X = B for m columns by FGMRES; returns info
 // x0: X holds an initial guess (else the solve starts from zero)
 void solve_block(mwi_problem* P, const double2* B, double2* X, int m, mwi_solve_info* info, bool x0 = false);
@@ -1369,17 +1375,29 @@ mwi_status mwi_forward_solve(mwi_problem_t P, const mwi_antenna* tx, int32_t n_t
         MWI_REQUIRE(n_tx >= 1 && n_rx >= 1 && n_tx <= 4096 && n_rx <= 4096, MWI_EINVAL, "bad antenna count");
         const Topology& T = P->mesh->T;
         cudaStream_t st = P->st;
-        map_antennas(T, tx, n_tx, P->tx_dof, P->tx_sign);
-        map_antennas(T, rx, n_rx, P->rx_dof, P->rx_sign);
         const int m = n_tx;
         const int64_t nm = T.ndof * (int64_t)m;
-        P->tx_dof_d.upload(P->tx_dof, st);
-        P->tx_sign_d.upload(P->tx_sign, st);
-        P->rx_dof_d.upload(P->rx_dof, st);
-        P->rx_sign_d.upload(P->rx_sign, st);
-        std::vector<double2> cur(m);
-        for (int j = 0; j < m; ++j) cur[j] = make_double2(tx[j].re_I, tx[j].im_I);
-        P->cur_d.upload(cur, st);
+        // the edge of an antenna depends only on the mesh and the antenna (a
+        // nearest-vertex search over the whole mesh): a call with the same
+        // antennas as the previous one (every step of an inversion) keeps the
+        // map and its device copies
+        if (!same_antennas(P->tx_key, tx, n_tx)) {
+            P->tx_key.clear();
+            map_antennas(T, tx, n_tx, P->tx_dof, P->tx_sign);
+            P->tx_dof_d.upload(P->tx_dof, st);
+            P->tx_sign_d.upload(P->tx_sign, st);
+            std::vector<double2> cur(m);
+            for (int j = 0; j < m; ++j) cur[j] = make_double2(tx[j].re_I, tx[j].im_I);
+            P->cur_d.upload(cur, st);
+            P->tx_key.assign(tx, tx + n_tx);
+        }
+        if (!same_antennas(P->rx_key, rx, n_rx)) {
+            P->rx_key.clear();
+            map_antennas(T, rx, n_rx, P->rx_dof, P->rx_sign);
+            P->rx_dof_d.upload(P->rx_dof, st);
+            P->rx_sign_d.upload(P->rx_sign, st);
+            P->rx_key.assign(rx, rx + n_rx);
+        }
         P->Brhs.ensure(nm);
         P->U.ensure(nm);
         MWI_CUDA(cudaMemsetAsync(P->Brhs.p, 0, nm * sizeof(double2), st));

@@ -268,3 +268,23 @@ def test_s_and_gradient_entrywise_by_db_bins(lib, precision, engine, rtol):
     J, grad = P.misfit_and_gradient(S_meas)
     assert np.abs(grad - grad_o).max() <= C * rtol * np.abs(grad_o).max()
     P.close()
+
+
+def test_antenna_map_reuse_follows_the_antennas(lib):
+    """A forward solve with the same antennas as the previous one reuses the
+    antenna-to-edge map; any change (other transmitters, reordered receivers,
+    other currents) maps again: every S equals a fresh problem's, bit for bit."""
+    case = chamber_case(12, 11, n_ant=8)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    tx2 = tx.copy()
+    tx2[:, 6:8] *= -1.5
+    calls = [(tx, rx), (tx, rx), (tx[:3], rx[::-1]), (tx[:3], rx), (tx2, rx), (tx, rx)]
+    P = lib.Problem(M, eps, FREQ, n_sub=4, precision=1, rtol=1e-9)
+    got = [P.forward_solve(t, r) for t, r in calls]
+    P.close()
+    for (t, r), S in zip(calls, got):
+        Q = lib.Problem(M, eps, FREQ, n_sub=4, precision=1, rtol=1e-9)
+        assert np.array_equal(S, Q.forward_solve(t, r))
+        Q.close()
+    assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[5])
+    M.close()
