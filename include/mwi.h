@@ -403,6 +403,19 @@ mwi_status mwi_coarse_prolongation_host(const double* fxyz, int64_t fnv, const i
                                         int64_t* nc, int64_t* nnz, int64_t* p_rp, int32_t* p_col, double* p_val,
                                         int32_t* fkind, int64_t* fverts, int32_t* ckind, int64_t* cverts);
 
+/* Host-only form of the antenna map of mwi_forward_solve (no device work),
+ * for checking it without a GPU: the mesh as mwi_mesh_create takes it; for
+ * every antenna (the mwi_antenna rule) the DOF id of its edge in the library's
+ * DOF numbering (dof_out [n_ant]) and its sign (sign_out [n_ant]: +1 when dir
+ * agrees with the edge's orientation from the lower to the higher vertex id,
+ * else -1); *ndof and the DOF keys (kind [ndof], verts [3 ndof]) as
+ * mwi_mesh_dof_keys gives them.  MWI_EINVAL for an antenna whose edge is a
+ * removed PEC edge, a zero or non-finite dir or a non-finite pos.  Call with
+ * null arrays to get *ndof; every array may be NULL. */
+mwi_status mwi_antenna_map_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                                const int32_t* bface_tag, int32_t order, const mwi_antenna* ants, int32_t n_ant,
+                                int32_t* dof_out, double* sign_out, int64_t* ndof, int32_t* kind, int64_t* verts);
+
 /* Sizes of the problem's coarse space (all 0 without one): n_c coarse DOFs,
  * entries of P and of A_c, host+device setup time of the last (re)build of
  * A_c and its factors, and the factorisation's replaced pivots.  Any pointer

@@ -843,49 +843,6 @@ void create_problem(mwi_mesh* M, const double* eps, bool eps_dev, double freq, c
     *out = P.release();
 }
 
-void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<int32_t>& dof,
-                  std::vector<double>& sign) {
-    dof.resize(n);
-    sign.resize(n);
-    for (int k = 0; k < n; ++k) {
-        const double* pos = a[k].pos;
-        const double* dir = a[k].dir;
-        const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
-        MWI_REQUIRE(dn > 0 && std::isfinite(dn), MWI_EINVAL, "antenna direction must be non-zero");
-        int64_t best_v = -1;
-        double best_d = 0;
-        for (int64_t v = 0; v < T.nv; ++v) {
-            double d = 0;
-            for (int q = 0; q < 3; ++q) {
-                double x = T.xyz[3 * v + q] - pos[q];
-                d += x * x;
-            }
-            if (best_v < 0 || d < best_d) { best_v = v; best_d = d; }
-        }
-        int32_t best_e = -1;
-        double best_c = -2;
-        for (int32_t q = T.v2e_ptr[best_v]; q < T.v2e_ptr[best_v + 1]; ++q) {
-            const int32_t e = T.v2e[q];
-            const int64_t o = T.edges[2 * e] == best_v ? T.edges[2 * e + 1] : T.edges[2 * e];
-            double vec[3], nv = 0, dot = 0;
-            for (int d = 0; d < 3; ++d) {
-                vec[d] = T.xyz[3 * o + d] - T.xyz[3 * best_v + d];
-                nv += vec[d] * vec[d];
-                dot += vec[d] * dir[d];
-            }
-            const double c = dot / (std::sqrt(nv) * dn);
-            if (c > best_c) { best_c = c; best_e = e; }
-        }
-        MWI_REQUIRE(best_e >= 0, MWI_EINVAL, "antenna vertex has no edge");
-        MWI_REQUIRE(T.edge_dof[best_e] >= 0, MWI_EINVAL, "antenna falls on a PEC edge");
-        double t = 0;
-        for (int d = 0; d < 3; ++d)
-            t += (T.xyz[3 * (int64_t)T.edges[2 * best_e + 1] + d] - T.xyz[3 * (int64_t)T.edges[2 * best_e] + d]) * dir[d];
-        dof[k] = T.edge_dof[best_e];
-        sign[k] = t > 0 ? 1.0 : -1.0;
-    }
-}
-
 // the same antennas, byte for byte, as the key
 bool same_antennas(const std::vector<mwi_antenna>& key, const mwi_antenna* a, int n) {
     return (int64_t)key.size() == n && std::memcmp(key.data(), a, n * sizeof(mwi_antenna)) == 0;
@@ -1938,6 +1895,25 @@ mwi_status mwi_coarse_prolongation_host(const double* fxyz, int64_t fnv, const i
         if (fverts) std::copy(Tf.dof_verts.begin(), Tf.dof_verts.end(), fverts);
         if (ckind) std::copy(Tc.dof_kind.begin(), Tc.dof_kind.end(), ckind);
         if (cverts) std::copy(Tc.dof_verts.begin(), Tc.dof_verts.end(), cverts);
+    });
+}
+
+mwi_status mwi_antenna_map_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                                const int32_t* bface_tag, int32_t order, const mwi_antenna* ants, int32_t n_ant,
+                                int32_t* dof_out, double* sign_out, int64_t* ndof, int32_t* kind, int64_t* verts) {
+    return guard([&] {
+        MWI_REQUIRE(xyz && tet && bface_tag, MWI_EINVAL, "null mesh array");
+        MWI_REQUIRE(n_ant >= 0 && (n_ant == 0 || ants), MWI_EINVAL, "null antennas");
+        Topology T;
+        build_topology(T, xyz, nv, tet, nt, bface_tag, order);
+        std::vector<int32_t> dof;
+        std::vector<double> sign;
+        map_antennas(T, ants, n_ant, dof, sign);
+        if (dof_out) std::copy(dof.begin(), dof.end(), dof_out);
+        if (sign_out) std::copy(sign.begin(), sign.end(), sign_out);
+        if (ndof) *ndof = T.ndof;
+        if (kind) std::copy(T.dof_kind.begin(), T.dof_kind.end(), kind);
+        if (verts) std::copy(T.dof_verts.begin(), T.dof_verts.end(), verts);
     });
 }
 

@@ -5,7 +5,10 @@
 #include <stdint.h>
 #include <vector_types.h>
 
+#include <cmath>
 #include <vector>
+
+#include "../../include/mwi.h"
 
 namespace mwi {
 
@@ -25,6 +28,24 @@ inline int pack_idx(int i, int j, int nl) {
     if (i > j) { int t = i; i = j; j = t; }
     return i * nl - i * (i - 1) / 2 + (j - i);
 }
+
+// Uniform grid of the mesh vertices for nearest-vertex queries (antenna.cpp):
+// cells of about two vertices over the bounding box, the vertices of a cell in
+// ascending id.
+struct VertexGrid {
+    double lo[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+    int64_t n[3] = {1, 1, 1};
+    double margin2 = 0;             // squared-distance slack of the search's stopping test
+    std::vector<int64_t> cell_ptr;  // [cells + 1]
+    std::vector<int32_t> ids;       // [nv]
+    // cell of coordinate x on axis a, clamped to the grid
+    int64_t cell_of(int a, double x) const {
+        const double t = std::floor((x - lo[a]) / h[a]);
+        if (!(t >= 0)) return 0;
+        if (t >= (double)(n[a] - 1)) return n[a] - 1;
+        return (int64_t)t;
+    }
+};
 
 struct Topology {
     int order = 1;
@@ -51,10 +72,19 @@ struct Topology {
     std::vector<int32_t> v2e_ptr, v2e;  // vertex -> incident edges (ascending edge id)
     std::vector<int32_t> v2t_ptr, v2t;  // vertex -> incident tets
     std::vector<int32_t> d2t_ptr, d2t;  // DOF -> (tet*nl + local) incidences, ascending tet
+    VertexGrid vgrid;                   // the vertices by grid cell
 };
 
 void build_topology(Topology& T, const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
                     const int32_t* bface_tag, int order);
+
+// antenna.cpp: the vertex grid; the vertex nearest to p (squared distance
+// summed over x, y, z in that order, lowest id on ties; -1 for no vertex); the
+// edge DOF and sign of every antenna
+void build_vertex_grid(const std::vector<double>& xyz, int64_t nv, VertexGrid& G);
+int64_t nearest_vertex(const std::vector<double>& xyz, const VertexGrid& G, const double* p);
+void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<int32_t>& dof,
+                  std::vector<double>& sign);
 
 // A sparse symmetric pattern with the list of element contributions of every
 // stored entry ("slot").  A contribution is encoded in an int64:

@@ -309,6 +309,7 @@ void build_topology(Topology& T, const double* xyz, int64_t nv, const int32_t* t
             }
         build_csr(T.ndof, key, val, T.d2t_ptr, T.d2t);
     }
+    build_vertex_grid(T.xyz, nv, T.vgrid);
 }
 
 }  // namespace mwi

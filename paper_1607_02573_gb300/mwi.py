@@ -93,6 +93,8 @@ _SIGS = {
     "mwi_coarse_prolongation_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, _dp, C.c_int64, _i32p,
                                      C.c_int64, _i32p, _i64p, _i64p, _i64p, _i64p, _i32p, _dp, _i32p, _i64p, _i32p,
                                      _i64p],
+    "mwi_antenna_map_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.POINTER(mwi_antenna), C.c_int32,
+                             _i32p, _dp, _i64p, _i32p, _i64p],
 }
 EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
@@ -147,6 +149,27 @@ def coarse_prolongation_host(fine, coarse, fine_order=1):
                                        _ptr(col, C.c_int32), _ptr(val, C.c_double), _ptr(fk, C.c_int32),
                                        _ptr(fv, C.c_int64), _ptr(ck, C.c_int32), _ptr(cv, C.c_int64)))
     return sp.csr_matrix((val, col, rp), shape=(n.value, nc.value)), (fk, fv), (ck, cv)
+
+
+def antenna_map_host(mesh, antennas, order=1):
+    """The antenna -> (edge DOF, sign) map of the forward solve for a mesh
+    (xyz, tet, bface_tag), computed on the host (mwi_antenna_map_host):
+    (dof [n], sign [n], (kind, verts) DOF keys of the library's numbering)."""
+    x = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    t = np.ascontiguousarray(mesh.tet, dtype=np.int32)
+    b = np.ascontiguousarray(mesh.bface_tag, dtype=np.int32)
+    a = _antennas(antennas)
+    n = len(a)
+    head = [_ptr(x, C.c_double), x.shape[0], _ptr(t, C.c_int32), t.shape[0], _ptr(b, C.c_int32), order, a, n]
+    ndof = C.c_int64()
+    check(mwi_antenna_map_host(*head, None, None, C.byref(ndof), None, None))
+    dof = np.empty(n, dtype=np.int32)
+    sign = np.empty(n, dtype=np.float64)
+    kind = np.empty(ndof.value, dtype=np.int32)
+    verts = np.empty((ndof.value, 3), dtype=np.int64)
+    check(mwi_antenna_map_host(*head, _ptr(dof, C.c_int32), _ptr(sign, C.c_double), C.byref(ndof),
+                               _ptr(kind, C.c_int32), _ptr(verts, C.c_int64)))
+    return dof, sign, (kind, verts)
 
 
 def normalised_weights(S_empty):
