@@ -57,9 +57,9 @@ def lbfgs_invert(problem, eps0, tx, rx, S_meas, w=None, iters=10, lr=1.0, histor
         eps = torch.complex(x[0], x[1])
         J = MisfitGrad.apply(eps, problem, tx, rx, S_meas, w)
         J.backward()
-        values.append(float(J))
+        values.append(float(J.detach()))
         if callback:
-            callback(len(values), float(J))
+            callback(len(values), values[-1])
         return J
 
     opt.step(closure)
