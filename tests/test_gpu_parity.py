@@ -288,3 +288,36 @@ def test_antenna_map_reuse_follows_the_antennas(lib):
         Q.close()
     assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[5])
     M.close()
+
+
+@pytest.mark.parametrize("precision,rtol,tol,max_steps", [(0, 1e-12, 1e-8, 2), (1, 1e-9, 1e-6, 6)])
+def test_degenerate_inputs(lib, precision, rtol, tol, max_steps):
+    """One transmitter against five receivers (S is 5 x 1); a transmitter with
+    zero current among others (its field and S column are exactly zero, and the
+    other columns are bit for bit those of the solve without it); one subdomain
+    (the ORAS preconditioner is then the factorised operator itself, B_1 = A:
+    one or two FGMRES steps in FP64, a few with the FP32 factors)."""
+    case = chamber_case(12, 11, n_ant=8)
+    mesh, eps, tx, rx, M, topo, perm = _setup(lib, case)
+    ref = O.forward(mesh.xyz, topo, eps, FREQ, tx, rx)
+    P = lib.Problem(M, eps, FREQ, n_sub=4, precision=precision, rtol=rtol)
+    S1 = P.forward_solve(tx[2:3], rx[:5])
+    assert S1.shape == (5, 1)
+    assert rel_err(S1, ref["S"][:5, 2:3]) <= tol
+    assert col_rel_err(P.fields_host(0), ref["U"][perm][:, 2:3]).max() <= tol
+    tz = tx.copy()
+    tz[3, 6:8] = 0.0
+    Sz = P.forward_solve(tz, rx)
+    U = P.fields_host(0)
+    assert np.all(U[:, 3] == 0) and np.all(Sz[:, 3] == 0)
+    keep = [0, 1, 2, 4, 5, 6, 7]
+    assert np.array_equal(Sz[:, keep], P.forward_solve(tx[keep], rx))
+    P.close()
+    P = lib.Problem(M, eps, FREQ, n_sub=1, precision=precision, rtol=rtol)
+    S = P.forward_solve(tx, rx)
+    info = P.info.as_dict()
+    assert info["n_converged"] == 8 and 1 <= info["iters_max"] <= max_steps, info
+    assert rel_err(S, ref["S"]) <= tol
+    assert col_rel_err(P.fields_host(0), ref["U"][perm]).max() <= tol
+    P.close()
+    M.close()
