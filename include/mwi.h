@@ -416,6 +416,28 @@ mwi_status mwi_antenna_map_host(const double* xyz, int64_t nv, const int32_t* te
                                 const int32_t* bface_tag, int32_t order, const mwi_antenna* ants, int32_t n_ant,
                                 int32_t* dof_out, double* sign_out, int64_t* ndof, int32_t* kind, int64_t* verts);
 
+/* Host-only form of the decomposition of Section 3 (no device work), for
+ * checking its host logic without a GPU: the mesh as mwi_mesh_create takes
+ * it, and n_sub, overlap and nd_leaf as in mwi_solver_opts (0: the defaults).
+ * Out (every pointer may be NULL; call with null arrays to get the sizes):
+ * part [nt] the non-overlapping partition; sub_off [n_sub+1] offsets of each
+ * subdomain's local rows in loc2glob [nloc] (global DOF ids, the subdomain's
+ * nested-dissection order) and dweight [nloc] (the partition-of-unity weight
+ * D_i of each local row, Eq. algebPartUnity); fu_off [n_sub+1] offsets of each
+ * subdomain's boundary face uses (the faces of T_i^delta with no neighbour in
+ * T_i^delta that are not PEC: the outer impedance faces and the interface
+ * faces that carry the impedance condition of B_i) in fu_verts [3 nfu] (the
+ * face's sorted vertex ids) and fu_tet [nfu] (the tet of T_i^delta owning it);
+ * *nloc, *nfu, *ndof and the DOF keys (kind [ndof], verts [3 ndof]) as
+ * mwi_mesh_dof_keys gives them; *factor_entries and *upd_rows, the
+ * multifrontal factor's entries (sum f p) and update rows (sum u). */
+mwi_status mwi_decomposition_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                                  const int32_t* bface_tag, int32_t order, int32_t n_sub, int32_t overlap,
+                                  int32_t nd_leaf, int32_t* part, int64_t* sub_off, int32_t* loc2glob,
+                                  double* dweight, int64_t* fu_off, int32_t* fu_verts, int32_t* fu_tet,
+                                  int64_t* nloc, int64_t* nfu, int64_t* ndof, int32_t* kind, int64_t* verts,
+                                  int64_t* factor_entries, int64_t* upd_rows);
+
 /* Sizes of the problem's coarse space (all 0 without one): n_c coarse DOFs,
  * entries of P and of A_c, host+device setup time of the last (re)build of
  * A_c and its factors, and the factorisation's replaced pivots.  Any pointer

@@ -1917,6 +1917,45 @@ mwi_status mwi_antenna_map_host(const double* xyz, int64_t nv, const int32_t* te
     });
 }
 
+mwi_status mwi_decomposition_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                                  const int32_t* bface_tag, int32_t order, int32_t n_sub, int32_t overlap,
+                                  int32_t nd_leaf, int32_t* part, int64_t* sub_off, int32_t* loc2glob,
+                                  double* dweight, int64_t* fu_off, int32_t* fu_verts, int32_t* fu_tet,
+                                  int64_t* nloc, int64_t* nfu, int64_t* ndof, int32_t* kind, int64_t* verts,
+                                  int64_t* factor_entries, int64_t* upd_rows) {
+    return guard([&] {
+        MWI_REQUIRE(xyz && tet && bface_tag, MWI_EINVAL, "null mesh array");
+        mwi_solver_opts o;
+        std::memset(&o, 0, sizeof(o));
+        o.n_sub = n_sub;
+        o.overlap = overlap;
+        o.nd_leaf = nd_leaf;
+        o = defaults(&o);
+        Topology T;
+        build_topology(T, xyz, nv, tet, nt, bface_tag, order);
+        MWI_REQUIRE(o.n_sub <= T.nt, MWI_EINVAL, "more subdomains than tets");
+        Decomposition D;
+        build_decomposition(T, nullptr, o.n_sub, o.overlap, o.nd_leaf, D);
+        const FaceUses& F = D.B_faces;
+        if (part) std::copy(D.part.begin(), D.part.end(), part);
+        if (sub_off) std::copy(D.sub_off.begin(), D.sub_off.end(), sub_off);
+        if (loc2glob) std::copy(D.loc2glob.begin(), D.loc2glob.end(), loc2glob);
+        if (dweight) std::copy(D.dweight.begin(), D.dweight.end(), dweight);
+        if (fu_off) std::copy(D.fu_off.begin(), D.fu_off.end(), fu_off);
+        if (fu_verts)
+            for (size_t k = 0; k < F.face.size(); ++k)
+                for (int j = 0; j < 3; ++j) fu_verts[3 * k + j] = T.faces[3 * (int64_t)F.face[k] + j];
+        if (fu_tet) std::copy(F.tet.begin(), F.tet.end(), fu_tet);
+        if (nloc) *nloc = (int64_t)D.loc2glob.size();
+        if (nfu) *nfu = (int64_t)F.face.size();
+        if (ndof) *ndof = T.ndof;
+        if (kind) std::copy(T.dof_kind.begin(), T.dof_kind.end(), kind);
+        if (verts) std::copy(T.dof_verts.begin(), T.dof_verts.end(), verts);
+        if (factor_entries) *factor_entries = D.factor_entries;
+        if (upd_rows) *upd_rows = D.upd_rows;
+    });
+}
+
 mwi_status mwi_coarse_info(mwi_problem_t P, int64_t* n_coarse, int64_t* nnz_p, int64_t* nnz_ac, double* setup_ms,
                            int32_t* n_perturbed) {
     return guard([&] {

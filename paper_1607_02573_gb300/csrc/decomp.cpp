@@ -366,6 +366,7 @@ void build_decomposition(const Topology& T, const int32_t* part_in, int n_sub, i
     D.B.row_ptr.assign(1, 0);
     D.B.slot_ptr.assign(1, 0);
     D.B_faces = FaceUses();
+    D.fu_off.assign(n_sub + 1, 0);
     D.fronts.clear();
     D.urows.clear();
     D.urel.clear();
@@ -400,6 +401,7 @@ void build_decomposition(const Topology& T, const int32_t* part_in, int n_sub, i
         }
         D.B_faces.face.insert(D.B_faces.face.end(), W.fu.face.begin(), W.fu.face.end());
         D.B_faces.tet.insert(D.B_faces.tet.end(), W.fu.tet.begin(), W.fu.tet.end());
+        D.fu_off[i + 1] = (int64_t)D.B_faces.face.size();
         const int32_t front_base = (int32_t)D.fronts.size();
         for (size_t k = 0; k < W.sym.fronts.size(); ++k) {
             const LocalFront& L = W.sym.fronts[k];

@@ -132,6 +132,7 @@ struct Decomposition {
     std::vector<double> own_w;          // their weights
     SlotMatrix B;                       // block-diagonal B_i in local ND numbering
     FaceUses B_faces;
+    std::vector<int64_t> fu_off;        // [n_sub+1] offsets of each subdomain's face uses in B_faces
     // multifrontal structure
     std::vector<Front> fronts;          // creation order: per subdomain, children before parents
     std::vector<int32_t> level_ptr;     // [n_levels+1] into level_fronts, deepest level first

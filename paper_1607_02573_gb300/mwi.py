@@ -95,6 +95,9 @@ _SIGS = {
                                      _i64p],
     "mwi_antenna_map_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.POINTER(mwi_antenna), C.c_int32,
                              _i32p, _dp, _i64p, _i32p, _i64p],
+    "mwi_decomposition_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                               _i32p, _i64p, _i32p, _dp, _i64p, _i32p, _i32p, _i64p, _i64p, _i64p, _i32p, _i64p,
+                               _i64p, _i64p],
 }
 EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
@@ -170,6 +173,35 @@ def antenna_map_host(mesh, antennas, order=1):
     check(mwi_antenna_map_host(*head, _ptr(dof, C.c_int32), _ptr(sign, C.c_double), C.byref(ndof),
                                _ptr(kind, C.c_int32), _ptr(verts, C.c_int64)))
     return dof, sign, (kind, verts)
+
+
+def decomposition_host(mesh, n_sub, overlap=0, nd_leaf=0, order=1):
+    """The ORAS decomposition of a mesh (xyz, tet, bface_tag), computed on the
+    host (mwi_decomposition_host); overlap and nd_leaf as in the solver options
+    (0: defaults).  Returns a dict: part [nt], sub_off [n_sub+1], loc2glob,
+    dweight [nloc], fu_off [n_sub+1], fu_verts [nfu, 3], fu_tet [nfu], kind,
+    verts (DOF keys), factor_entries, upd_rows."""
+    x = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    t = np.ascontiguousarray(mesh.tet, dtype=np.int32)
+    b = np.ascontiguousarray(mesh.bface_tag, dtype=np.int32)
+    head = [_ptr(x, C.c_double), x.shape[0], _ptr(t, C.c_int32), t.shape[0], _ptr(b, C.c_int32), order, n_sub,
+            overlap, nd_leaf]
+    nloc, nfu, ndof, fe, ur = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    sizes = [C.byref(nloc), C.byref(nfu), C.byref(ndof)]
+    check(mwi_decomposition_host(*head, *([None] * 7), *sizes, None, None, None, None))
+    ns = int(n_sub) if n_sub > 0 else 64
+    out = dict(part=np.empty(t.shape[0], dtype=np.int32), sub_off=np.empty(ns + 1, dtype=np.int64),
+               loc2glob=np.empty(nloc.value, dtype=np.int32), dweight=np.empty(nloc.value, dtype=np.float64),
+               fu_off=np.empty(ns + 1, dtype=np.int64), fu_verts=np.empty((nfu.value, 3), dtype=np.int32),
+               fu_tet=np.empty(nfu.value, dtype=np.int32), kind=np.empty(ndof.value, dtype=np.int32),
+               verts=np.empty((ndof.value, 3), dtype=np.int64))
+    check(mwi_decomposition_host(*head, _ptr(out["part"], C.c_int32), _ptr(out["sub_off"], C.c_int64),
+                                 _ptr(out["loc2glob"], C.c_int32), _ptr(out["dweight"], C.c_double),
+                                 _ptr(out["fu_off"], C.c_int64), _ptr(out["fu_verts"], C.c_int32),
+                                 _ptr(out["fu_tet"], C.c_int32), *sizes, _ptr(out["kind"], C.c_int32),
+                                 _ptr(out["verts"], C.c_int64), C.byref(fe), C.byref(ur)))
+    out["factor_entries"], out["upd_rows"] = fe.value, ur.value
+    return out
 
 
 def normalised_weights(S_empty):
