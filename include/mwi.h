@@ -438,6 +438,18 @@ mwi_status mwi_decomposition_host(const double* xyz, int64_t nv, const int32_t* 
                                   int64_t* nloc, int64_t* nfu, int64_t* ndof, int32_t* kind, int64_t* verts,
                                   int64_t* factor_entries, int64_t* upd_rows);
 
+/* Host-only form of the multifrontal structure of the decomposition (the
+ * same arguments as mwi_decomposition_host): *n_fronts fronts over all
+ * subdomains, children before parents, with front_info [5 n_fronts] = (sub,
+ * start, p, u, parent) per front (start: first pivot, local nested-dissection
+ * index; p pivots; u update rows; parent: front id or -1), u_off [n_fronts]
+ * offsets of each front's update-row list in urows [*n_urows] (local
+ * nested-dissection indices of ancestor pivots, ascending).  Every pointer may
+ * be NULL; call with null arrays to get the sizes. */
+mwi_status mwi_fronts_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt, const int32_t* bface_tag,
+                           int32_t order, int32_t n_sub, int32_t overlap, int32_t nd_leaf, int32_t* n_fronts,
+                           int64_t* n_urows, int32_t* front_info, int64_t* u_off, int32_t* urows);
+
 /* Sizes of the problem's coarse space (all 0 without one): n_c coarse DOFs,
  * entries of P and of A_c, host+device setup time of the last (re)build of
  * A_c and its factors, and the factorisation's replaced pivots.  Any pointer

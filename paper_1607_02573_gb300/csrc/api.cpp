@@ -1917,6 +1917,48 @@ mwi_status mwi_antenna_map_host(const double* xyz, int64_t nv, const int32_t* te
     });
 }
 
+// the library's decomposition of a host mesh (the solver options' defaults for
+// zero arguments), for the host-only entry points
+static void host_decomposition(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                               const int32_t* bface_tag, int32_t order, int32_t n_sub, int32_t overlap,
+                               int32_t nd_leaf, Topology& T, Decomposition& D) {
+    MWI_REQUIRE(xyz && tet && bface_tag, MWI_EINVAL, "null mesh array");
+    mwi_solver_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.n_sub = n_sub;
+    o.overlap = overlap;
+    o.nd_leaf = nd_leaf;
+    o = defaults(&o);
+    build_topology(T, xyz, nv, tet, nt, bface_tag, order);
+    MWI_REQUIRE(o.n_sub <= T.nt, MWI_EINVAL, "more subdomains than tets");
+    build_decomposition(T, nullptr, o.n_sub, o.overlap, o.nd_leaf, D);
+}
+
+mwi_status mwi_fronts_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt, const int32_t* bface_tag,
+                           int32_t order, int32_t n_sub, int32_t overlap, int32_t nd_leaf, int32_t* n_fronts,
+                           int64_t* n_urows, int32_t* front_info, int64_t* u_off, int32_t* urows) {
+    return guard([&] {
+        Topology T;
+        Decomposition D;
+        host_decomposition(xyz, nv, tet, nt, bface_tag, order, n_sub, overlap, nd_leaf, T, D);
+        if (n_fronts) *n_fronts = (int32_t)D.fronts.size();
+        if (n_urows) *n_urows = (int64_t)D.urows.size();
+        for (size_t k = 0; k < D.fronts.size(); ++k) {
+            const Front& F = D.fronts[k];
+            if (front_info) {
+                int32_t* q = front_info + 5 * k;
+                q[0] = F.sub;
+                q[1] = F.start;
+                q[2] = F.p;
+                q[3] = F.u;
+                q[4] = F.parent;
+            }
+            if (u_off) u_off[k] = F.u_off;
+        }
+        if (urows) std::copy(D.urows.begin(), D.urows.end(), urows);
+    });
+}
+
 mwi_status mwi_decomposition_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
                                   const int32_t* bface_tag, int32_t order, int32_t n_sub, int32_t overlap,
                                   int32_t nd_leaf, int32_t* part, int64_t* sub_off, int32_t* loc2glob,
@@ -1924,18 +1966,9 @@ mwi_status mwi_decomposition_host(const double* xyz, int64_t nv, const int32_t* 
                                   int64_t* nloc, int64_t* nfu, int64_t* ndof, int32_t* kind, int64_t* verts,
                                   int64_t* factor_entries, int64_t* upd_rows) {
     return guard([&] {
-        MWI_REQUIRE(xyz && tet && bface_tag, MWI_EINVAL, "null mesh array");
-        mwi_solver_opts o;
-        std::memset(&o, 0, sizeof(o));
-        o.n_sub = n_sub;
-        o.overlap = overlap;
-        o.nd_leaf = nd_leaf;
-        o = defaults(&o);
         Topology T;
-        build_topology(T, xyz, nv, tet, nt, bface_tag, order);
-        MWI_REQUIRE(o.n_sub <= T.nt, MWI_EINVAL, "more subdomains than tets");
         Decomposition D;
-        build_decomposition(T, nullptr, o.n_sub, o.overlap, o.nd_leaf, D);
+        host_decomposition(xyz, nv, tet, nt, bface_tag, order, n_sub, overlap, nd_leaf, T, D);
         const FaceUses& F = D.B_faces;
         if (part) std::copy(D.part.begin(), D.part.end(), part);
         if (sub_off) std::copy(D.sub_off.begin(), D.sub_off.end(), sub_off);

@@ -98,6 +98,8 @@ _SIGS = {
     "mwi_decomposition_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                _i32p, _i64p, _i32p, _dp, _i64p, _i32p, _i32p, _i64p, _i64p, _i64p, _i32p, _i64p,
                                _i64p, _i64p],
+    "mwi_fronts_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _i32p,
+                        _i64p, _i32p, _i64p, _i32p],
 }
 EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
@@ -202,6 +204,24 @@ def decomposition_host(mesh, n_sub, overlap=0, nd_leaf=0, order=1):
                                  _ptr(out["verts"], C.c_int64), C.byref(fe), C.byref(ur)))
     out["factor_entries"], out["upd_rows"] = fe.value, ur.value
     return out
+
+
+def fronts_host(mesh, n_sub, overlap=0, nd_leaf=0, order=1):
+    """The multifrontal structure of the decomposition (mwi_fronts_host):
+    (info [n_fronts, 5] = (sub, start, p, u, parent), u_off [n_fronts], urows)."""
+    x = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    t = np.ascontiguousarray(mesh.tet, dtype=np.int32)
+    b = np.ascontiguousarray(mesh.bface_tag, dtype=np.int32)
+    head = [_ptr(x, C.c_double), x.shape[0], _ptr(t, C.c_int32), t.shape[0], _ptr(b, C.c_int32), order, n_sub,
+            overlap, nd_leaf]
+    nf, nu = C.c_int32(), C.c_int64()
+    check(mwi_fronts_host(*head, C.byref(nf), C.byref(nu), None, None, None))
+    info = np.empty((nf.value, 5), dtype=np.int32)
+    u_off = np.empty(nf.value, dtype=np.int64)
+    urows = np.empty(nu.value, dtype=np.int32)
+    check(mwi_fronts_host(*head, C.byref(nf), C.byref(nu), _ptr(info, C.c_int32), _ptr(u_off, C.c_int64),
+                          _ptr(urows, C.c_int32)))
+    return info, u_off, urows
 
 
 def normalised_weights(S_empty):

@@ -66,3 +66,74 @@ def test_bad_decomposition_arguments_are_refused():
         mwi.decomposition_host(mesh, 10 ** 6)
     with pytest.raises(mwi.MwiError, match="MWI_EINVAL"):
         mwi.decomposition_host(mesh, 4, overlap=9)
+
+
+def _elimination_structure(n, adj):
+    """struct(L[:, k]) of the LDL^T factor of a matrix with the symmetric
+    graph adj (lists of neighbours, no self loops) eliminated in the order
+    0..n-1: the neighbours above k plus the structures of k's children in the
+    elimination tree (Liu's row-merge form of symbolic factorisation)."""
+    kids = [[] for _ in range(n)]
+    out = []
+    for k in range(n):
+        s = {j for j in adj[k] if j > k}
+        for c in kids[k]:
+            s |= out[c]
+        s.discard(k)
+        out.append(s)
+        if s:
+            kids[min(s)].append(k)
+    return out
+
+
+@pytest.mark.parametrize("case,order,n_sub,leaf", [("chamber", 1, 4, 16), ("cube", 2, 2, 32)])
+def test_fronts_cover_the_elimination_fill(case, order, n_sub, leaf):
+    """The multifrontal structure of every subdomain: the fronts' pivots tile
+    the local rows; a front's update rows are ancestors' pivots, ascending, and
+    lie in its parent's front (the extend-add's premise); the root fronts have
+    none; and every column's fill in the exact symbolic LDL^T of the graph of
+    B_i (DOFs coupled through a tet of T_i^delta) in the nested-dissection
+    order lies in the rows of the column's front."""
+    mesh = chamber_mesh(10, 9) if case == "chamber" else cube_mesh(4)
+    lib = mwi.decomposition_host(mesh, n_sub, nd_leaf=leaf, order=order)
+    info, u_off, urows = mwi.fronts_host(mesh, n_sub, nd_leaf=leaf, order=order)
+    topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, order)
+    perm = key_perm(lib["kind"], lib["verts"], topo)
+    part = dd.rcb_partition(mesh.xyz, mesh.tet, n_sub)
+    dec = dd.Decomposition(mesh.xyz, mesh.tet, topo, part, 1)
+    for i in range(n_sub):
+        a, b = lib["sub_off"][i], lib["sub_off"][i + 1]
+        n = b - a
+        g2l = -np.ones(topo.ndof, dtype=np.int64)
+        g2l[perm[lib["loc2glob"][a:b]]] = np.arange(n)
+        adj = [set() for _ in range(n)]
+        for t in np.nonzero(dec.Td[i])[0]:
+            d = topo.tet_dofs[t]
+            loc = g2l[d[d >= 0]]
+            for x in loc:
+                adj[x].update(loc.tolist())
+        for k in range(n):
+            adj[k].discard(k)
+        fill = _elimination_structure(n, adj)
+        ids = np.nonzero(info[:, 0] == i)[0]
+        fr = info[ids]
+        order_ = np.argsort(fr[:, 1])
+        starts, ps = fr[order_, 1], fr[order_, 2]
+        assert starts[0] == 0 and np.array_equal(starts[1:], (starts + ps)[:-1]) and starts[-1] + ps[-1] == n
+        rows_of = {}
+        for f, (sub, start, p, u, parent) in zip(ids, fr):
+            U = urows[u_off[f]:u_off[f] + u]
+            assert np.all(np.diff(U) > 0) and (u == 0 or U[0] >= start + p)
+            rows_of[f] = (start, p, set(U.tolist()))
+            if parent < 0:
+                assert u == 0
+            else:
+                assert parent > f and info[parent, 0] == i
+        for f, (start, p, U) in rows_of.items():
+            parent = info[f, 4]
+            if parent >= 0:
+                ps_, pp, pU = rows_of[parent]
+                assert U <= set(range(ps_, ps_ + pp)) | pU
+            front_rows = set(range(start, start + p)) | U
+            for k in range(start, start + p):
+                assert fill[k] <= front_rows, (i, f, k)
