@@ -1,10 +1,10 @@
-// Antenna -> edge map of the right-hand sides and the receiver functionals
-// (Section 2: a transmitting or receiving antenna is an edge-current dipole on
-// one mesh edge).  The edge starts at the mesh vertex nearest to the antenna's
-// position (lowest vertex id on ties) and is, among the edges at that vertex,
-// the one best aligned with the antenna's direction (largest cosine; lowest
-// edge id on ties); its sign says whether the direction agrees with the edge's
-// orientation (low -> high vertex id).
+// Antenna -> edge map of the right-hand sides and the receiver functionals.
+// The waveguide ports of Section 2 (Eq. eqwgj) are read as edge-current
+// dipoles, one mesh edge per antenna.  The edge starts at the mesh vertex
+// nearest to the antenna's position (lowest vertex id on ties) and is, among
+// the edges at that vertex, the one best aligned with the antenna's direction
+// (largest cosine; lowest edge id on ties); its sign says whether the
+// direction agrees with the edge's orientation (low -> high vertex id).
 //
 // The nearest vertex comes from a uniform grid of the vertices, searched in
 // shells of cells around the position's cell until no unsearched cell can
