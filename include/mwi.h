@@ -450,6 +450,22 @@ mwi_status mwi_fronts_host(const double* xyz, int64_t nv, const int32_t* tet, in
                            int32_t order, int32_t n_sub, int32_t overlap, int32_t nd_leaf, int32_t* n_fronts,
                            int64_t* n_urows, int32_t* front_info, int64_t* u_off, int32_t* urows);
 
+/* Host-only form of the assembly map of A (no device work): the pattern of A
+ * in CSR (row_ptr [ndof+1], col [nnz]) in the library's DOF numbering and, per
+ * stored entry, its element contributions in summation order (slot_ptr
+ * [nnz+1], contrib [ncontrib]: bits 0..15 the packed local pair (i <= j:
+ * i nl - i (i-1)/2 + j - i), bits 16..61 the tet id or face-use id, bit 62
+ * set for a face use); the local DOFs of every tet (tet_dofs [nt nl], -1 for
+ * a removed PEC DOF, nl = 6 or 20) and of every face use (fu_dofs [nfu nlf],
+ * nlf = 3 or 8) with its owning tet (fu_tet [nfu]) and sorted vertex ids
+ * (fu_verts [3 nfu]); *ndof and the DOF keys (kind [ndof], verts [3 ndof]).
+ * The device assembly sums exactly these contributions in this order.  Every
+ * pointer may be NULL; call with null arrays to get the sizes. */
+mwi_status mwi_slots_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt, const int32_t* bface_tag,
+                          int32_t order, int64_t* ndof, int64_t* nnz, int64_t* ncontrib, int64_t* nfu,
+                          int64_t* row_ptr, int32_t* col, int64_t* slot_ptr, int64_t* contrib, int32_t* tet_dofs,
+                          int32_t* fu_dofs, int32_t* fu_tet, int32_t* fu_verts, int32_t* kind, int64_t* verts);
+
 /* Sizes of the problem's coarse space (all 0 without one): n_c coarse DOFs,
  * entries of P and of A_c, host+device setup time of the last (re)build of
  * A_c and its factors, and the factorisation's replaced pivots.  Any pointer

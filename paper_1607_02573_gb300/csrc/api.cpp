@@ -1989,6 +1989,39 @@ mwi_status mwi_decomposition_host(const double* xyz, int64_t nv, const int32_t* 
     });
 }
 
+mwi_status mwi_slots_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt, const int32_t* bface_tag,
+                          int32_t order, int64_t* ndof, int64_t* nnz, int64_t* ncontrib, int64_t* nfu,
+                          int64_t* row_ptr, int32_t* col, int64_t* slot_ptr, int64_t* contrib, int32_t* tet_dofs,
+                          int32_t* fu_dofs, int32_t* fu_tet, int32_t* fu_verts, int32_t* kind, int64_t* verts) {
+    return guard([&] {
+        MWI_REQUIRE(xyz && tet && bface_tag, MWI_EINVAL, "null mesh array");
+        Topology T;
+        build_topology(T, xyz, nv, tet, nt, bface_tag, order);
+        SlotMatrix A;
+        FaceUses F;
+        build_global_slots(T, A, F);
+        if (ndof) *ndof = T.ndof;
+        if (nnz) *nnz = (int64_t)A.col.size();
+        if (ncontrib) *ncontrib = (int64_t)A.contrib.size();
+        if (nfu) *nfu = (int64_t)F.face.size();
+        if (row_ptr) std::copy(A.row_ptr.begin(), A.row_ptr.end(), row_ptr);
+        if (col) std::copy(A.col.begin(), A.col.end(), col);
+        if (slot_ptr) std::copy(A.slot_ptr.begin(), A.slot_ptr.end(), slot_ptr);
+        if (contrib) std::copy(A.contrib.begin(), A.contrib.end(), contrib);
+        if (tet_dofs) std::copy(T.tet_dofs.begin(), T.tet_dofs.end(), tet_dofs);
+        for (size_t k = 0; k < F.face.size(); ++k) {
+            const int64_t f = F.face[k];
+            if (fu_dofs)
+                for (int i = 0; i < T.nlf; ++i) fu_dofs[(int64_t)T.nlf * k + i] = T.face_dofs[(int64_t)T.nlf * f + i];
+            if (fu_verts)
+                for (int j = 0; j < 3; ++j) fu_verts[3 * k + j] = T.faces[3 * f + j];
+        }
+        if (fu_tet) std::copy(F.tet.begin(), F.tet.end(), fu_tet);
+        if (kind) std::copy(T.dof_kind.begin(), T.dof_kind.end(), kind);
+        if (verts) std::copy(T.dof_verts.begin(), T.dof_verts.end(), verts);
+    });
+}
+
 mwi_status mwi_coarse_info(mwi_problem_t P, int64_t* n_coarse, int64_t* nnz_p, int64_t* nnz_ac, double* setup_ms,
                            int32_t* n_perturbed) {
     return guard([&] {

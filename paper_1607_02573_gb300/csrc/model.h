@@ -89,8 +89,8 @@ void map_antennas(const Topology& T, const mwi_antenna* a, int n, std::vector<in
 // A sparse symmetric pattern with the list of element contributions of every
 // stored entry ("slot").  A contribution is encoded in an int64:
 //   bits 0..15  packed local pair index
-//   bits 16..62 entity (tet id, or face-use id)
-//   bit 63      1 for a face-use contribution
+//   bits 16..61 entity (tet id, or face-use id)
+//   bit 62      1 for a face-use contribution (kFaceFlag)
 struct SlotMatrix {
     int64_t nrows = 0;
     std::vector<int64_t> row_ptr;   // [nrows+1]

@@ -100,6 +100,8 @@ _SIGS = {
                                _i64p, _i64p],
     "mwi_fronts_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _i32p,
                         _i64p, _i32p, _i64p, _i32p],
+    "mwi_slots_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, _i64p, _i64p, _i64p, _i64p, _i64p, _i32p,
+                       _i64p, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p],
 }
 EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
@@ -222,6 +224,31 @@ def fronts_host(mesh, n_sub, overlap=0, nd_leaf=0, order=1):
     check(mwi_fronts_host(*head, C.byref(nf), C.byref(nu), _ptr(info, C.c_int32), _ptr(u_off, C.c_int64),
                           _ptr(urows, C.c_int32)))
     return info, u_off, urows
+
+
+def slots_host(mesh, order=1):
+    """The assembly map of A (mwi_slots_host) as a dict: row_ptr, col,
+    slot_ptr, contrib, tet_dofs [nt, nl], fu_dofs [nfu, nlf], fu_tet, fu_verts
+    [nfu, 3], kind, verts."""
+    x = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    t = np.ascontiguousarray(mesh.tet, dtype=np.int32)
+    b = np.ascontiguousarray(mesh.bface_tag, dtype=np.int32)
+    head = [_ptr(x, C.c_double), x.shape[0], _ptr(t, C.c_int32), t.shape[0], _ptr(b, C.c_int32), order]
+    n, nnz, nc, nfu = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    sizes = [C.byref(n), C.byref(nnz), C.byref(nc), C.byref(nfu)]
+    check(mwi_slots_host(*head, *sizes, *([None] * 10)))
+    nl, nlf = (6, 3) if order == 1 else (20, 8)
+    out = dict(row_ptr=np.empty(n.value + 1, dtype=np.int64), col=np.empty(nnz.value, dtype=np.int32),
+               slot_ptr=np.empty(nnz.value + 1, dtype=np.int64), contrib=np.empty(nc.value, dtype=np.int64),
+               tet_dofs=np.empty((t.shape[0], nl), dtype=np.int32), fu_dofs=np.empty((nfu.value, nlf), dtype=np.int32),
+               fu_tet=np.empty(nfu.value, dtype=np.int32), fu_verts=np.empty((nfu.value, 3), dtype=np.int32),
+               kind=np.empty(n.value, dtype=np.int32), verts=np.empty((n.value, 3), dtype=np.int64))
+    check(mwi_slots_host(*head, *sizes, _ptr(out["row_ptr"], C.c_int64), _ptr(out["col"], C.c_int32),
+                         _ptr(out["slot_ptr"], C.c_int64), _ptr(out["contrib"], C.c_int64),
+                         _ptr(out["tet_dofs"], C.c_int32), _ptr(out["fu_dofs"], C.c_int32),
+                         _ptr(out["fu_tet"], C.c_int32), _ptr(out["fu_verts"], C.c_int32),
+                         _ptr(out["kind"], C.c_int32), _ptr(out["verts"], C.c_int64)))
+    return out
 
 
 def normalised_weights(S_empty):
