@@ -12,6 +12,7 @@
 // search's, in O(cells searched) instead of O(vertices) per antenna.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "common.h"
 #include "model.h"
