@@ -466,6 +466,27 @@ mwi_status mwi_slots_host(const double* xyz, int64_t nv, const int32_t* tet, int
                           int64_t* row_ptr, int32_t* col, int64_t* slot_ptr, int64_t* contrib, int32_t* tet_dofs,
                           int32_t* fu_dofs, int32_t* fu_tet, int32_t* fu_verts, int32_t* kind, int64_t* verts);
 
+/* Host-only form of the local operators' assembly maps (the same mesh and
+ * decomposition arguments as mwi_decomposition_host): the block-diagonal
+ * pattern of the B_i (B_row_ptr [nloc+1] over the concatenated local rows of
+ * mwi_decomposition_host's loc2glob, B_col [nslot] the column's local
+ * nested-dissection index within its subdomain), each stored entry's
+ * contributions in summation order (B_slot_ptr [nslot+1], B_contrib
+ * [ncontrib], encoded as in mwi_slots_host, face-use ids indexing the face
+ * uses of mwi_decomposition_host) and the face uses' face-local DOFs (fu_dofs
+ * [nfu nlf]); and the map that assembles the fronts from them
+ * (amap_front_ptr [n_fronts+1] over the fronts of mwi_fronts_host,
+ * amap_slot [namap] the stored entry, amap_pos [namap] its position in the
+ * factor store: the front's panel offset (sum of (p+u) p over the fronts
+ * before it) + pivot column * (p+u) + front row).  Every pointer may be NULL;
+ * call with null arrays to get the sizes. */
+mwi_status mwi_local_assembly_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                                   const int32_t* bface_tag, int32_t order, int32_t n_sub, int32_t overlap,
+                                   int32_t nd_leaf, int64_t* nloc, int64_t* nslot, int64_t* ncontrib, int64_t* nfu,
+                                   int64_t* namap, int32_t* n_fronts, int64_t* B_row_ptr, int32_t* B_col,
+                                   int64_t* B_slot_ptr, int64_t* B_contrib, int32_t* fu_dofs,
+                                   int64_t* amap_front_ptr, int64_t* amap_slot, int64_t* amap_pos);
+
 /* Sizes of the problem's coarse space (all 0 without one): n_c coarse DOFs,
  * entries of P and of A_c, host+device setup time of the last (re)build of
  * A_c and its factors, and the factorisation's replaced pivots.  Any pointer

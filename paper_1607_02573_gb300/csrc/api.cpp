@@ -2022,6 +2022,37 @@ mwi_status mwi_slots_host(const double* xyz, int64_t nv, const int32_t* tet, int
     });
 }
 
+mwi_status mwi_local_assembly_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt,
+                                   const int32_t* bface_tag, int32_t order, int32_t n_sub, int32_t overlap,
+                                   int32_t nd_leaf, int64_t* nloc, int64_t* nslot, int64_t* ncontrib, int64_t* nfu,
+                                   int64_t* namap, int32_t* n_fronts, int64_t* B_row_ptr, int32_t* B_col,
+                                   int64_t* B_slot_ptr, int64_t* B_contrib, int32_t* fu_dofs,
+                                   int64_t* amap_front_ptr, int64_t* amap_slot, int64_t* amap_pos) {
+    return guard([&] {
+        Topology T;
+        Decomposition D;
+        host_decomposition(xyz, nv, tet, nt, bface_tag, order, n_sub, overlap, nd_leaf, T, D);
+        const SlotMatrix& B = D.B;
+        if (nloc) *nloc = B.nrows;
+        if (nslot) *nslot = (int64_t)B.col.size();
+        if (ncontrib) *ncontrib = (int64_t)B.contrib.size();
+        if (nfu) *nfu = (int64_t)D.B_faces.face.size();
+        if (namap) *namap = (int64_t)D.amap_slot.size();
+        if (n_fronts) *n_fronts = (int32_t)D.fronts.size();
+        if (B_row_ptr) std::copy(B.row_ptr.begin(), B.row_ptr.end(), B_row_ptr);
+        if (B_col) std::copy(B.col.begin(), B.col.end(), B_col);
+        if (B_slot_ptr) std::copy(B.slot_ptr.begin(), B.slot_ptr.end(), B_slot_ptr);
+        if (B_contrib) std::copy(B.contrib.begin(), B.contrib.end(), B_contrib);
+        if (fu_dofs)
+            for (size_t k = 0; k < D.B_faces.face.size(); ++k)
+                for (int i = 0; i < T.nlf; ++i)
+                    fu_dofs[(int64_t)T.nlf * k + i] = T.face_dofs[(int64_t)T.nlf * D.B_faces.face[k] + i];
+        if (amap_front_ptr) std::copy(D.amap_front_ptr.begin(), D.amap_front_ptr.end(), amap_front_ptr);
+        if (amap_slot) std::copy(D.amap_slot.begin(), D.amap_slot.end(), amap_slot);
+        if (amap_pos) std::copy(D.amap_pos.begin(), D.amap_pos.end(), amap_pos);
+    });
+}
+
 mwi_status mwi_coarse_info(mwi_problem_t P, int64_t* n_coarse, int64_t* nnz_p, int64_t* nnz_ac, double* setup_ms,
                            int32_t* n_perturbed) {
     return guard([&] {

@@ -102,6 +102,9 @@ _SIGS = {
                         _i64p, _i32p, _i64p, _i32p],
     "mwi_slots_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, _i64p, _i64p, _i64p, _i64p, _i64p, _i32p,
                        _i64p, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p],
+    "mwi_local_assembly_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                _i64p, _i64p, _i64p, _i64p, _i64p, _i32p, _i64p, _i32p, _i64p, _i64p, _i32p, _i64p,
+                                _i64p, _i64p],
 }
 EXPORTED = sorted(list(_SIGS) + ["mwi_last_error", "mwi_launch_count", "mwi_device_alloc_count"])
 
@@ -248,6 +251,32 @@ def slots_host(mesh, order=1):
                          _ptr(out["tet_dofs"], C.c_int32), _ptr(out["fu_dofs"], C.c_int32),
                          _ptr(out["fu_tet"], C.c_int32), _ptr(out["fu_verts"], C.c_int32),
                          _ptr(out["kind"], C.c_int32), _ptr(out["verts"], C.c_int64)))
+    return out
+
+
+def local_assembly_host(mesh, n_sub, overlap=0, nd_leaf=0, order=1):
+    """The local operators' assembly maps (mwi_local_assembly_host) as a dict:
+    B_row_ptr, B_col, B_slot_ptr, B_contrib, fu_dofs [nfu, nlf],
+    amap_front_ptr, amap_slot, amap_pos."""
+    x = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    t = np.ascontiguousarray(mesh.tet, dtype=np.int32)
+    b = np.ascontiguousarray(mesh.bface_tag, dtype=np.int32)
+    head = [_ptr(x, C.c_double), x.shape[0], _ptr(t, C.c_int32), t.shape[0], _ptr(b, C.c_int32), order, n_sub,
+            overlap, nd_leaf]
+    nloc, nslot, nc, nfu, nam = (C.c_int64() for _ in range(5))
+    nf = C.c_int32()
+    sizes = [C.byref(nloc), C.byref(nslot), C.byref(nc), C.byref(nfu), C.byref(nam), C.byref(nf)]
+    check(mwi_local_assembly_host(*head, *sizes, *([None] * 8)))
+    nlf = 3 if order == 1 else 8
+    out = dict(B_row_ptr=np.empty(nloc.value + 1, dtype=np.int64), B_col=np.empty(nslot.value, dtype=np.int32),
+               B_slot_ptr=np.empty(nslot.value + 1, dtype=np.int64), B_contrib=np.empty(nc.value, dtype=np.int64),
+               fu_dofs=np.empty((nfu.value, nlf), dtype=np.int32),
+               amap_front_ptr=np.empty(nf.value + 1, dtype=np.int64), amap_slot=np.empty(nam.value, dtype=np.int64),
+               amap_pos=np.empty(nam.value, dtype=np.int64))
+    check(mwi_local_assembly_host(*head, *sizes, *(_ptr(out[k], C.c_int32 if out[k].dtype == np.int32 else C.c_int64)
+                                                   for k in ("B_row_ptr", "B_col", "B_slot_ptr", "B_contrib",
+                                                             "fu_dofs", "amap_front_ptr", "amap_slot",
+                                                             "amap_pos"))))
     return out
 
 
