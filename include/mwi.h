@@ -444,11 +444,18 @@ mwi_status mwi_decomposition_host(const double* xyz, int64_t nv, const int32_t* 
  * start, p, u, parent) per front (start: first pivot, local nested-dissection
  * index; p pivots; u update rows; parent: front id or -1), u_off [n_fronts]
  * offsets of each front's update-row list in urows [*n_urows] (local
- * nested-dissection indices of ancestor pivots, ascending).  Every pointer may
- * be NULL; call with null arrays to get the sizes. */
+ * nested-dissection indices of ancestor pivots, ascending) and urel
+ * [*n_urows] (each update row's position among its parent's front rows:
+ * pivots, then update rows).  The extend-add table of the sweeps: for front
+ * row t of front s (index sum over the fronts before s of p + u, plus t),
+ * asm_ptr [sum (p+u) + 1] delimits in asm_src [*n_asm] the rows of the update
+ * buffer (front c's update row j is row sum over the fronts before c of u,
+ * plus j) that add into it, children ascending.  Every pointer may be NULL;
+ * call with null arrays to get the sizes. */
 mwi_status mwi_fronts_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt, const int32_t* bface_tag,
                            int32_t order, int32_t n_sub, int32_t overlap, int32_t nd_leaf, int32_t* n_fronts,
-                           int64_t* n_urows, int32_t* front_info, int64_t* u_off, int32_t* urows);
+                           int64_t* n_urows, int64_t* n_asm, int32_t* front_info, int64_t* u_off, int32_t* urows,
+                           int32_t* urel, int64_t* asm_ptr, int32_t* asm_src);
 
 /* Host-only form of the assembly map of A (no device work): the pattern of A
  * in CSR (row_ptr [ndof+1], col [nnz]) in the library's DOF numbering and, per

@@ -1936,7 +1936,8 @@ static void host_decomposition(const double* xyz, int64_t nv, const int32_t* tet
 
 mwi_status mwi_fronts_host(const double* xyz, int64_t nv, const int32_t* tet, int64_t nt, const int32_t* bface_tag,
                            int32_t order, int32_t n_sub, int32_t overlap, int32_t nd_leaf, int32_t* n_fronts,
-                           int64_t* n_urows, int32_t* front_info, int64_t* u_off, int32_t* urows) {
+                           int64_t* n_urows, int64_t* n_asm, int32_t* front_info, int64_t* u_off, int32_t* urows,
+                           int32_t* urel, int64_t* asm_ptr, int32_t* asm_src) {
     return guard([&] {
         Topology T;
         Decomposition D;
@@ -1956,6 +1957,10 @@ mwi_status mwi_fronts_host(const double* xyz, int64_t nv, const int32_t* tet, in
             if (u_off) u_off[k] = F.u_off;
         }
         if (urows) std::copy(D.urows.begin(), D.urows.end(), urows);
+        if (n_asm) *n_asm = (int64_t)D.asm_src.size();
+        if (urel) std::copy(D.urel.begin(), D.urel.end(), urel);
+        if (asm_ptr) std::copy(D.asm_ptr.begin(), D.asm_ptr.end(), asm_ptr);
+        if (asm_src) std::copy(D.asm_src.begin(), D.asm_src.end(), asm_src);
     });
 }
 

@@ -99,7 +99,7 @@ _SIGS = {
                                _i32p, _i64p, _i32p, _dp, _i64p, _i32p, _i32p, _i64p, _i64p, _i64p, _i32p, _i64p,
                                _i64p, _i64p],
     "mwi_fronts_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _i32p,
-                        _i64p, _i32p, _i64p, _i32p],
+                        _i64p, _i64p, _i32p, _i64p, _i32p, _i32p, _i64p, _i32p],
     "mwi_slots_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, _i64p, _i64p, _i64p, _i64p, _i64p, _i32p,
                        _i64p, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p, _i64p],
     "mwi_local_assembly_host": [_dp, C.c_int64, _i32p, C.c_int64, _i32p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -212,21 +212,27 @@ def decomposition_host(mesh, n_sub, overlap=0, nd_leaf=0, order=1):
 
 
 def fronts_host(mesh, n_sub, overlap=0, nd_leaf=0, order=1):
-    """The multifrontal structure of the decomposition (mwi_fronts_host):
-    (info [n_fronts, 5] = (sub, start, p, u, parent), u_off [n_fronts], urows)."""
+    """The multifrontal structure of the decomposition (mwi_fronts_host) as a
+    dict: info [n_fronts, 5] = (sub, start, p, u, parent), u_off [n_fronts],
+    urows, urel, asm_ptr, asm_src."""
     x = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
     t = np.ascontiguousarray(mesh.tet, dtype=np.int32)
     b = np.ascontiguousarray(mesh.bface_tag, dtype=np.int32)
     head = [_ptr(x, C.c_double), x.shape[0], _ptr(t, C.c_int32), t.shape[0], _ptr(b, C.c_int32), order, n_sub,
             overlap, nd_leaf]
-    nf, nu = C.c_int32(), C.c_int64()
-    check(mwi_fronts_host(*head, C.byref(nf), C.byref(nu), None, None, None))
-    info = np.empty((nf.value, 5), dtype=np.int32)
-    u_off = np.empty(nf.value, dtype=np.int64)
-    urows = np.empty(nu.value, dtype=np.int32)
-    check(mwi_fronts_host(*head, C.byref(nf), C.byref(nu), _ptr(info, C.c_int32), _ptr(u_off, C.c_int64),
-                          _ptr(urows, C.c_int32)))
-    return info, u_off, urows
+    nf, nu, na = C.c_int32(), C.c_int64(), C.c_int64()
+    sizes = [C.byref(nf), C.byref(nu), C.byref(na)]
+    check(mwi_fronts_host(*head, *sizes, *([None] * 6)))
+    out = dict(info=np.empty((nf.value, 5), dtype=np.int32), u_off=np.empty(nf.value, dtype=np.int64),
+               urows=np.empty(nu.value, dtype=np.int32), urel=np.empty(nu.value, dtype=np.int32))
+    check(mwi_fronts_host(*head, *sizes, _ptr(out["info"], C.c_int32), _ptr(out["u_off"], C.c_int64),
+                          _ptr(out["urows"], C.c_int32), _ptr(out["urel"], C.c_int32), None, None))
+    nrows = int((out["info"][:, 2].astype(np.int64) + out["info"][:, 3]).sum())
+    out["asm_ptr"] = np.empty(nrows + 1, dtype=np.int64)
+    out["asm_src"] = np.empty(na.value, dtype=np.int32)
+    check(mwi_fronts_host(*head, *sizes, None, None, None, None, _ptr(out["asm_ptr"], C.c_int64),
+                          _ptr(out["asm_src"], C.c_int32)))
+    return out
 
 
 def slots_host(mesh, order=1):

@@ -96,7 +96,8 @@ def test_fronts_cover_the_elimination_fill(case, order, n_sub, leaf):
     order lies in the rows of the column's front."""
     mesh = chamber_mesh(10, 9) if case == "chamber" else cube_mesh(4)
     lib = mwi.decomposition_host(mesh, n_sub, nd_leaf=leaf, order=order)
-    info, u_off, urows = mwi.fronts_host(mesh, n_sub, nd_leaf=leaf, order=order)
+    fh = mwi.fronts_host(mesh, n_sub, nd_leaf=leaf, order=order)
+    info, u_off, urows = fh["info"], fh["u_off"], fh["urows"]
     topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, order)
     perm = key_perm(lib["kind"], lib["verts"], topo)
     part = dd.rcb_partition(mesh.xyz, mesh.tet, n_sub)
@@ -134,6 +135,26 @@ def test_fronts_cover_the_elimination_fill(case, order, n_sub, leaf):
             if parent >= 0:
                 ps_, pp, pU = rows_of[parent]
                 assert U <= set(range(ps_, ps_ + pp)) | pU
+                # urel: each update row's position among the parent's front rows
+                prow = list(range(ps_, ps_ + pp)) + sorted(pU)
+                Ul = urows[u_off[f]:u_off[f] + info[f, 3]].tolist()
+                assert fh["urel"][u_off[f]:u_off[f] + info[f, 3]].tolist() == [prow.index(x) for x in Ul]
             front_rows = set(range(start, start + p)) | U
             for k in range(start, start + p):
                 assert fill[k] <= front_rows, (i, f, k)
+    # the sweeps' extend-add table: front row t of front s gathers, children
+    # ascending, the update-buffer rows of its children's update rows at t
+    f = info[:, 2].astype(np.int64) + info[:, 3]
+    base = np.concatenate([[0], np.cumsum(f)])
+    upd = np.concatenate([[0], np.cumsum(info[:, 3].astype(np.int64))])
+    want = [[] for _ in range(int(base[-1]))]
+    for c in range(info.shape[0]):
+        s_ = info[c, 4]
+        if s_ < 0:
+            continue
+        for j in range(info[c, 3]):
+            want[base[s_] + fh["urel"][u_off[c] + j]].append(int(upd[c] + j))
+    ap, src = fh["asm_ptr"], fh["asm_src"]
+    assert ap.size == base[-1] + 1
+    for r in range(int(base[-1])):
+        assert src[ap[r]:ap[r + 1]].tolist() == want[r]

@@ -42,7 +42,8 @@ def test_local_assembly_and_front_maps(case, order, n_sub):
         eps = cube_eps(mesh.xyz, mesh.tet)
     eps = np.asarray(eps)
     dl = mwi.decomposition_host(mesh, n_sub, order=order)
-    info, u_off, urows = mwi.fronts_host(mesh, n_sub, order=order)
+    fh = mwi.fronts_host(mesh, n_sub, order=order)
+    info, u_off, urows = fh["info"], fh["u_off"], fh["urows"]
     la = mwi.local_assembly_host(mesh, n_sub, order=order)
     td = mwi.slots_host(mesh, order)["tet_dofs"]
     topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, order)
