@@ -50,3 +50,9 @@ def rel_err(a, b):
 
 def col_rel_err(a, b):
     return np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0)
+
+
+def unpack_pairs(nl):
+    """(i, j), i <= j, of every packed local pair index i nl - i (i-1)/2 + j - i
+    of the library's element contributions."""
+    return {i * nl - i * (i - 1) // 2 + (j - i): (i, j) for i in range(nl) for j in range(i, nl)}

@@ -24,19 +24,12 @@ from oracle.assemble import impedance_faces
 from oracle.constants import k0_of
 from oracle.topology import LOCAL_FACES
 from synthetic import chamber_eps, chamber_mesh, cube_eps, cube_mesh
-from tests._helpers import FREQ, key_perm
+from tests._helpers import FREQ, key_perm, unpack_pairs
 
 mwi = pytest.importorskip("paper_1607_02573_gb300.mwi")
 
 FACE_FLAG = 1 << 62
 
-
-def _unpack_table(nl):
-    tab = {}
-    for i in range(nl):
-        for j in range(i, nl):
-            tab[i * nl - i * (i - 1) // 2 + (j - i)] = (i, j)
-    return tab
 
 
 @pytest.mark.parametrize("case,order", [("chamber", 1), ("chamber", 2), ("cube", 1), ("cube", 2)])
@@ -83,7 +76,7 @@ def test_slot_map_reproduces_the_oracle_assembly(case, order):
     fu_local = np.array([[list(td[t]).index(d) if d >= 0 else -1 for d in fd]
                          for t, fd in zip(lib["fu_tet"], lib["fu_dofs"])]).reshape(lib["fu_tet"].size, -1)
 
-    tab_t, tab_f = _unpack_table(nl), _unpack_table(lib["fu_dofs"].shape[1])
+    tab_t, tab_f = unpack_pairs(nl), unpack_pairs(lib["fu_dofs"].shape[1])
     sp, contrib = lib["slot_ptr"], lib["contrib"]
     seen = {}
     lists = {}

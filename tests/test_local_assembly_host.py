@@ -21,15 +21,12 @@ from oracle import dd
 from oracle.constants import k0_of
 from oracle.topology import LOCAL_FACES
 from synthetic import chamber_eps, chamber_mesh, cube_eps, cube_mesh
-from tests._helpers import FREQ, key_perm
+from tests._helpers import FREQ, key_perm, unpack_pairs
 
 mwi = pytest.importorskip("paper_1607_02573_gb300.mwi")
 
 FACE_FLAG = 1 << 62
 
-
-def _unpack_table(nl):
-    return {i * nl - i * (i - 1) // 2 + (j - i): (i, j) for i in range(nl) for j in range(i, nl)}
 
 
 @pytest.mark.parametrize("case,order,n_sub", [("chamber", 1, 4), ("cube", 2, 3)])
@@ -60,7 +57,7 @@ def test_local_assembly_and_front_maps(case, order, n_sub):
     face = 1j * (k0 * np.sqrt(eps[fu_tet]))[:, None, None] * O.face_matrix(mesh.xyz, topo, fu_tet, lf)
     fu_local = np.array([[list(td[t]).index(d) if d >= 0 else -1 for d in fd]
                          for t, fd in zip(fu_tet, la["fu_dofs"])]).reshape(fu_tet.size, -1)
-    tab_t, tab_f = _unpack_table(topo.nl), _unpack_table(la["fu_dofs"].shape[1])
+    tab_t, tab_f = unpack_pairs(topo.nl), unpack_pairs(la["fu_dofs"].shape[1])
 
     rp, col = la["B_row_ptr"], la["B_col"]
     slot_row = np.repeat(np.arange(rp.size - 1), np.diff(rp))
