@@ -31,7 +31,6 @@ mwi = pytest.importorskip("paper_1607_02573_gb300.mwi")
 FACE_FLAG = 1 << 62
 
 
-
 @pytest.mark.parametrize("case,order", [("chamber", 1), ("chamber", 2), ("cube", 1), ("cube", 2)])
 def test_slot_map_reproduces_the_oracle_assembly(case, order):
     if case == "chamber":

@@ -28,7 +28,6 @@ mwi = pytest.importorskip("paper_1607_02573_gb300.mwi")
 FACE_FLAG = 1 << 62
 
 
-
 @pytest.mark.parametrize("case,order,n_sub", [("chamber", 1, 4), ("cube", 2, 3)])
 def test_local_assembly_and_front_maps(case, order, n_sub):
     if case == "chamber":
