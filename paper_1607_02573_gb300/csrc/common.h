@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <new>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -22,6 +23,29 @@ struct Error : public std::runtime_error {
 };
 
 void set_last_error(const std::string& msg);
+
+// Run the body of a C-ABI entry point: an Error becomes its status, a failed
+// host allocation MWI_ENOMEM, any other exception MWI_EINVAL; the message goes
+// to mwi_last_error.
+template <typename F>
+mwi_status guard(F&& f) {
+    try {
+        f();
+        return MWI_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return MWI_ENOMEM;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return MWI_EINVAL;
+    }
+}
+
+// The solver options with every zero field replaced by its default (api.cpp).
+mwi_solver_opts solver_defaults(const mwi_solver_opts* o);
 
 // kernels launched by this library (every launch site ends in MWI_CHECK_LAUNCH)
 extern std::atomic<int64_t> g_launches;
