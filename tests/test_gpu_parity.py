@@ -191,6 +191,11 @@ def test_errors_are_reported(lib):
     with pytest.raises(lib.MwiError) as e:
         P.misfit_and_gradient(np.zeros((4, 4), dtype=complex))
     assert e.value.status == lib.MWI_ESTATE
+    # empty and oversized antenna sets are refused before any device work
+    for t, r in [(tx[:0], rx), (tx, rx[:0]), (np.repeat(tx[:1], 4097, axis=0), rx)]:
+        with pytest.raises(lib.MwiError) as e:
+            P.forward_solve(t, r)
+        assert e.value.status == lib.MWI_EINVAL
     with pytest.raises(lib.MwiError) as e:
         M.close()
     assert e.value.status == lib.MWI_ESTATE
