@@ -4,7 +4,8 @@
 * reciprocity: S = S^T because the form is bilinear (A = A^T);
 * the adjoint identity, checked as <A^{-1} x, y> = <x, A^{-1} y> (unconjugated);
 * the adjoint gradient equals central finite differences of J with respect to
-  Re and Im of eps on sampled tets, including tets that own an impedance face;
+  Re and Im of eps on sampled tets, including tets that own an impedance face,
+  for first- and second-order elements;
 * J = 0 and grad = 0 when the measurements equal the simulation.
 """
 
@@ -17,9 +18,9 @@ from synthetic import antenna_array, chamber_mesh, cube_antennas, cube_eps, cube
 FREQ = 1e9
 
 
-def _cube_problem(n=4, seed=4):
+def _cube_problem(n=4, seed=4, order=1):
     mesh = cube_mesh(n)
-    topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, 1)
+    topo = O.build_topology(mesh.tet, mesh.bface_tag, mesh.nv, order)
     rng = np.random.default_rng(seed)
     eps = 44 - 20j + rng.uniform(-5, 5, mesh.nt) + 1j * rng.uniform(-3, 3, mesh.nt)
     tx = antenna_array(cube_antennas())
@@ -65,9 +66,9 @@ def test_adjoint_dot_identity():
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-@pytest.mark.parametrize("weighted", [False, True])
-def test_gradient_matches_finite_differences(weighted):
-    mesh, topo, eps, tx = _cube_problem()
+@pytest.mark.parametrize("weighted,order", [(False, 1), (True, 1), (True, 2)])
+def test_gradient_matches_finite_differences(weighted, order):
+    mesh, topo, eps, tx = _cube_problem(n=4 if order == 1 else 3, order=order)
     f0 = O.forward(mesh.xyz, topo, eps, FREQ, tx, tx)
     rng = np.random.default_rng(1)
     S_meas = f0["S"] * (1 + 0.3 * rng.standard_normal(f0["S"].shape)) + 0.1 * np.abs(f0["S"]).mean()
@@ -77,8 +78,10 @@ def test_gradient_matches_finite_differences(weighted):
     owners = np.unique(topo.face_tets[topo.face_tag == 2, 0])
     pick = [int(np.argmax(np.abs(grad))), int(rng.integers(mesh.nt)), int(owners[0]), int(owners[7])]
 
+    K, M = O.element_matrices(mesh.xyz, topo)
+
     def J_at(e):
-        f = O.forward(mesh.xyz, topo, e, FREQ, tx, tx)
+        f = O.forward(mesh.xyz, topo, e, FREQ, tx, tx, A=O.assemble_system(mesh.xyz, topo, e, FREQ, K=K, M=M))
         return O.misfit(f["S"], S_meas, w)[0]
 
     for t in pick:
